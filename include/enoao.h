@@ -1,0 +1,190 @@
+/*
+ * enoao.h -- C interface of the GB300 ENO-AO library.
+ *
+ * The library advances hyperbolic conservation laws u_t + f(u)_x = 0 (and
+ * their dimension-by-dimension extension to 2D and 3D) with the ENO schemes
+ * of adaptive order of H. Shen, "A class of ENO schemes with adaptive order
+ * for solving hyperbolic conservation laws" (arXiv 2108.12742):
+ *   - conservative finite-difference form L(u)_j = -(F_{j+1/2}-F_{j-1/2})/dx
+ *     (Sec. 2, Eq. 1DWENOFD), summed over the axes (Sec. 2);
+ *   - global Lax-Friedrichs splitting f^{+-} = (f +- alpha u)/2 (Sec. 2,
+ *     Eq. LF_Flux_Split), alpha the maximum of |f'(u)| over the mesh;
+ *   - for the Euler equations, projection onto characteristic fields with the
+ *     Roe average at each face (Sec. 4);
+ *   - ENO-AO interface values: candidate stencils from first order up to the
+ *     designed order 5 or 7, chosen by the indicator IS = MIN(delta_L,
+ *     delta_R) of Eq. (New_Smoothness_Indicator) and the selection principle
+ *     with threshold delta (Sec. 3.2, Tables 1, 4, 5, Appendix A);
+ *   - third-order TVD Runge-Kutta time stepping (Sec. 2).
+ * Every step of that path runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point:
+ *   - A state array U holds the conserved variables as a structure of arrays,
+ *     U[v][k][j][i] (i along x fastest, j along y, k along z), float64.  For
+ *     the Euler equations v = (rho, rho*u, [rho*v], [rho*w], rho*e), nv =
+ *     ndim + 2; for scalar advection nv = 1.
+ *   - Pointers flagged "on_device" point to CUDA device memory of the device
+ *     that was current at enoao_create; otherwise they point to host memory.
+ *     The library copies from and to the caller's buffers and never keeps a
+ *     caller pointer beyond the call.
+ *   - Work is ordered on the CUDA stream given at creation (0 = the legacy
+ *     default stream): a call's device work starts after the stream's earlier
+ *     work and the stream's later work sees its results.  Calls that return
+ *     data to the host, and enoao_advance*, synchronise before returning.
+ *   - No exception or abort crosses this interface: every failure returns a
+ *     status code and leaves a message readable with enoao_last_error.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef ENOAO_H
+#define ENOAO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct enoao_ctx enoao_ctx;
+
+typedef enum {
+  ENOAO_OK = 0,
+  ENOAO_EINVAL = 1,    /* invalid argument or configuration */
+  ENOAO_ENOMEM = 2,    /* device or host allocation failed */
+  ENOAO_ECUDA = 3,     /* a CUDA call failed (message has the CUDA error) */
+  ENOAO_ENONPHYS = 4,  /* non-physical state met: rho <= 0, p <= 0 or NaN */
+  ENOAO_ETIMEOUT = 5   /* a bounded device wait gave up */
+} enoao_status;
+
+enum { ENOAO_SCALAR_ADVECTION = 0, ENOAO_EULER = 1 };
+enum { ENOAO_PERIODIC = 0, ENOAO_TRANSMISSIVE = 1 };
+enum { ENOAO_FP64 = 0, ENOAO_FP32_BULK = 1 };
+
+typedef struct {
+  int ndim;        /* 1, 2 or 3 */
+  int system;      /* ENOAO_SCALAR_ADVECTION (f = adv_speed * u) or ENOAO_EULER */
+  int order;       /* designed order: 5 (ENO-AO5) or 7 (ENO-AO7) */
+  int precision;   /* ENOAO_FP64, or ENOAO_FP32_BULK: reconstruction, indicators
+                      and projections in FP32, state and Runge-Kutta
+                      accumulation in FP64, near-tie choices re-decided in FP64 */
+  int64_t n[3];    /* cells per axis; unused axes must be 1 */
+  double lo[3];    /* domain [lo, hi] per axis; dx = (hi - lo) / n */
+  double hi[3];
+  int bc[3];       /* ENOAO_PERIODIC or ENOAO_TRANSMISSIVE (zero-gradient) per axis */
+  int reserved;
+  double adv_speed;  /* scalar advection speed a */
+  double gamma;      /* ratio of specific heats (Euler) */
+  double delta;      /* selection threshold, 1e-5 in the paper (Sec. 3.2 remark) */
+  double tie_rel;    /* FP32_BULK: relative margin under which an indicator
+                        comparison is re-done in FP64 */
+} enoao_config;
+
+/* Run statistics of a context. */
+typedef struct {
+  double t;                   /* simulated time reached */
+  int64_t steps;              /* Runge-Kutta steps taken since enoao_init_state */
+  double alpha[3];            /* Lax-Friedrichs alpha per axis of the last step */
+  double dt;                  /* last step size */
+  uint64_t fp64_fallbacks;    /* FP32_BULK: indicator decisions re-done in FP64 */
+  uint64_t decisions;         /* stencil decisions taken (2 per field per face) */
+} enoao_stats;
+
+/* Fills a configuration with defaults: 1D, Euler, order 5, FP64, periodic,
+ * gamma 1.4, adv_speed 1, delta 1e-5, tie_rel 1e-3, one cell per axis. */
+void enoao_config_default(enoao_config *cfg);
+
+/* Creates a context for one problem and allocates its device memory (three
+ * state buffers and one right-hand-side buffer) on the current device.
+ * cuda_stream: a cudaStream_t (may be 0).  Errors: ENOAO_EINVAL for an
+ * invalid configuration (ndim not 1..3, order not 5 or 7, fewer cells along
+ * a swept axis than the stencil needs (11), non-positive dx, gamma <= 1,
+ * delta < 0), ENOAO_ENOMEM, ENOAO_ECUDA.  *out is NULL on failure. */
+enoao_status enoao_create(const enoao_config *cfg, void *cuda_stream, enoao_ctx **out);
+
+/* Creates a context for nprob independent 1D problems of uneven lengths n[i]
+ * on [lo[i], hi[i]] that share proto's system, order, precision, boundary
+ * conditions and constants; each problem keeps its own alpha and time step.
+ * States are concatenated: U[v][offset_i + i], offset_i = sum_{k<i} n[k].
+ * They advance together in one persistent launch (enoao_batch_advance_steps).
+ * Only 1D Euler or scalar problems; errors as enoao_create. */
+enoao_status enoao_batch_create(const enoao_config *proto, int nprob, const int64_t *n,
+                                const double *lo, const double *hi, void *cuda_stream,
+                                enoao_ctx **out);
+
+/* Releases every resource of the context (NULL is ignored). */
+void enoao_destroy(enoao_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none); valid until the
+ * next call on the context.  ctx may be NULL (message of the last failed
+ * create on this host thread). */
+const char *enoao_last_error(const enoao_ctx *ctx);
+
+/* Sets the state U^n (conserved variables, layout above) and resets time and
+ * step count.  Computes alpha of the new state.  ENOAO_ENONPHYS if the state
+ * has rho <= 0, p <= 0 or NaN (Euler). */
+enoao_status enoao_init_state(enoao_ctx *ctx, const double *U, int on_device);
+
+/* Copies the current state U^n out (same layout). */
+enoao_status enoao_get_state(enoao_ctx *ctx, double *U, int on_device);
+
+/* Interface fluxes F_{j+1/2} of Eq. (1DWENOFD) along axis dir for the current
+ * state, with alpha of the current state (Sec. 2, 3, 4).  Fhat has the state's
+ * layout with n[dir] replaced by n[dir]+1 faces; face f lies between cells
+ * f-1 and f (periodic: faces 0 and n[dir] coincide).  stencil_idx (may be
+ * NULL) receives the chosen candidate (priority index 0..8: S_j^j, S_j^{j+1},
+ * S_{j-1}^{j+1}, S_{j-2}^{j+1}, S_{j-1}^{j+2}, S_{j-2}^{j+2}, S_{j-3}^{j+2},
+ * S_{j-2}^{j+3}, S_{j-3}^{j+3}) per characteristic field v (Euler order:
+ * u-c, entropy, shear..., u+c), sign s (0: f^+, 1: f^-) and face at
+ * stencil_idx[(v*2 + s)*nfaces + face].  Not available for batched contexts. */
+enoao_status enoao_reconstruct_fluxes(enoao_ctx *ctx, int dir, double *Fhat,
+                                      int8_t *stencil_idx, int on_device);
+
+/* One stage (0, 1 or 2) of the third-order TVD Runge-Kutta step (Sec. 2):
+ *   stage 0: U1 = U^n + dt L(U^n)      (alpha recomputed from U^n)
+ *   stage 1: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
+ *   stage 2: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
+ * Stages must be called in order; after stage 2 the state is U^{n+1} and the
+ * step count and time advance by one step and dt. */
+enoao_status enoao_rk_stage(enoao_ctx *ctx, int stage, double dt);
+
+/* Advances to t_end with dt = cfl / sum_d(alpha_d / dx_d), alpha from U^n of
+ * each step, the last step shortened to land on t_end; or with the fixed
+ * step dt_fixed when dt_fixed > 0.  Stops after max_steps steps when
+ * max_steps > 0.  Steps run as CUDA-graph replays; alpha and dt never leave
+ * the device.  Returns the time reached and the steps taken (nullable). */
+enoao_status enoao_advance(enoao_ctx *ctx, double t_end, double cfl, double dt_fixed,
+                           int64_t max_steps, double *t_out, int64_t *steps_out);
+
+/* Advances exactly nsteps steps with dt = cfl / sum_d(alpha_d / dx_d) (no
+ * end time).  For batched contexts every problem takes nsteps steps with its
+ * own alpha and dt in one persistent launch. */
+enoao_status enoao_advance_steps(enoao_ctx *ctx, int64_t nsteps, double cfl);
+
+/* Same as enoao_advance_steps but only enqueues the work on the stream and
+ * returns without synchronising or reading the error word (for timing
+ * loops); check with enoao_sync. */
+enoao_status enoao_advance_steps_async(enoao_ctx *ctx, int64_t nsteps, double cfl);
+
+/* Waits for the context's work and reports ENOAO_ENONPHYS / ENOAO_ETIMEOUT
+ * raised by kernels since the last check. */
+enoao_status enoao_sync(enoao_ctx *ctx);
+
+/* Reads the run statistics (synchronises). */
+enoao_status enoao_get_stats(enoao_ctx *ctx, enoao_stats *out);
+
+/* Number of CUDA kernel launches one step issues (per graph replay step). */
+int enoao_launches_per_step(const enoao_ctx *ctx);
+
+/* Tile shape of the sweep kernels along each axis: lines per tile (ta) and
+ * faces per tile (ts).  Set by the autotuner or by hand; 0 keeps the current
+ * value.  Errors: ENOAO_EINVAL for shapes the kernels do not support. */
+enoao_status enoao_set_tiles(enoao_ctx *ctx, int dir, int ta, int ts);
+enoao_status enoao_get_tiles(const enoao_ctx *ctx, int dir, int *ta, int *ts);
+
+/* Times every supported tile shape of every axis on the current state
+ * (restored afterwards) with CUDA events and keeps the fastest. */
+enoao_status enoao_autotune(enoao_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENOAO_H */

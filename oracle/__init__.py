@@ -74,6 +74,7 @@ def _load():
                                       ctypes.POINTER(ctypes.c_byte), D]
             lib.or_rhs.argtypes = [P, D, D, D]
             lib.or_step.argtypes = [P, D, ctypes.c_double]
+            lib.or_step_alpha.argtypes = [P, D, ctypes.c_double, D]
             lib.or_advance.argtypes = [P, D, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_long,
                                        D, ctypes.POINTER(ctypes.c_long)]
@@ -198,6 +199,14 @@ def step(P, U, dt):
     st = _load().or_step(ctypes.byref(P), _dp(U), dt)
     if st:
         raise FloatingPointError("oracle: non-physical state")
+    return U
+
+
+def step_alpha(P, U, dt, alpha_vec):
+    """One step with the splitting constants of the full mesh given."""
+    U = _state(P, U).copy()
+    a = np.ascontiguousarray(alpha_vec, dtype=np.float64)
+    _load().or_step_alpha(ctypes.byref(P), _dp(U), dt, _dp(a))
     return U
 
 

@@ -417,13 +417,13 @@ int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
           int comp = perm_component(P->system, P->ndim, d, c);
           Fhat[comp * nfaces + fi] = Fh[f * nv + c];
         }
-        for (int c = 0; c < nv && (il || gl); ++c) {
-          int comp = perm_component(P->system, P->ndim, d, c);
+        /* choices are stored per characteristic field, in the order
+         * (u-c, entropy, shear..., u+c) for the Euler equations */
+        for (int c = 0; c < nv && (il || gl); ++c)
           for (int s = 0; s < 2; ++s) {
-            if (il) idx[(comp * 2 + s) * nfaces + fi] = il[(c * 2 + s) * (n + 1) + f];
-            if (gl) gap[(comp * 2 + s) * nfaces + fi] = gl[(c * 2 + s) * (n + 1) + f];
+            if (il) idx[(c * 2 + s) * nfaces + fi] = il[(c * 2 + s) * (n + 1) + f];
+            if (gl) gap[(c * 2 + s) * nfaces + fi] = gl[(c * 2 + s) * (n + 1) + f];
           }
-        }
       }
     }
     free(q);
@@ -490,11 +490,15 @@ int or_alpha(const or_problem *P, const double *U, double *alpha) {
 }
 
 int or_step(const or_problem *P, double *U, double dt) {
-  int nv = or_nvars(P);
-  long M = (long)nv * n_cells(P);
   double alpha[3];
   int st = or_alpha(P, U, alpha);
   if (st) return st;
+  return or_step_alpha(P, U, dt, alpha);
+}
+
+int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha) {
+  int nv = or_nvars(P);
+  long M = (long)nv * n_cells(P);
   double *u0 = malloc(sizeof(double) * M);
   double *L = malloc(sizeof(double) * M);
   memcpy(u0, U, sizeof(double) * M);

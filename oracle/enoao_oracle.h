@@ -66,8 +66,9 @@ int or_alpha(const or_problem *P, const double *U, double *alpha);
 
 /* Interface fluxes along axis d for state U with splitting constants alpha.
  * Fhat has the layout of U with n[d] replaced by n[d]+1 faces; face f sits
- * between cells f-1 and f.  idx (nullable) holds, per variable, sign (0:
- * f^+, 1: f^-) and face, the chosen candidate: idx[((v*2+s)*nf) + face]
+ * between cells f-1 and f.  idx (nullable) holds, per characteristic field
+ * v (u-c, entropy, shear..., u+c; the variable itself for scalars), sign s
+ * (0: f^+, 1: f^-) and face, the chosen candidate: idx[(v*2+s)*nf + face]
  * with nf the face count; gap (nullable) holds the decision gap likewise. */
 int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
               double *Fhat, signed char *idx, double *gap);
@@ -79,6 +80,11 @@ int or_rhs(const or_problem *P, const double *U, const double *alpha,
 /* One third-order TVD Runge-Kutta step of size dt, alpha taken from U at the
  * start of the step.  U is updated in place. */
 int or_step(const or_problem *P, double *U, double dt);
+
+/* The same step with the splitting constants alpha given (alpha is a
+ * property of the whole mesh, so a sub-block of a larger grid must be
+ * stepped with the full grid's alpha). */
+int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha);
 
 /* Advance to t_end.  dt = cfl / sum_d(alpha_d/dx_d) when dt_fixed <= 0,
  * else dt = dt_fixed; the last step is shortened to land on t_end.  Stops

@@ -1,0 +1,828 @@
+// Host runtime of the ENO-AO library: the C interface of include/enoao.h,
+// device buffers, the step kernels that keep alpha and dt on the device, CUDA
+// graph capture of whole steps, and the tile autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "enoao.h"
+#include "enoao_internal.h"
+
+using namespace enoao;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Batched-problem state (defined with the batch kernels).
+}  // namespace
+
+namespace enoao {
+struct BatchState;
+void batch_destroy(BatchState* b);
+enoao_status batch_create(enoao_ctx* ctx, const enoao_config* proto, int nprob,
+                          const int64_t* n, const double* lo, const double* hi);
+enoao_status batch_advance(enoao_ctx* ctx, int64_t nsteps, double cfl, bool sync);
+enoao_status batch_init_state(enoao_ctx* ctx, const double* U, int on_device);
+enoao_status batch_get_state(enoao_ctx* ctx, double* U, int on_device);
+}  // namespace enoao
+
+struct enoao_ctx {
+  enoao_config cfg{};
+  int nv = 0;
+  long long ncell = 0;
+  double dx[3] = {1, 1, 1};
+  cudaStream_t user = nullptr;   // caller's stream
+  cudaStream_t s = nullptr;      // library stream (non-blocking, capturable)
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, t0 = nullptr, t1 = nullptr;
+  double* U[3] = {nullptr, nullptr, nullptr};  // U^n, U1, U2
+  void* rhs = nullptr;
+  StepState* st = nullptr;       // device
+  StepState* st_host = nullptr;  // pinned mirror
+  int ta[3] = {0, 0, 0}, ts[3] = {0, 0, 0}, block[3] = {128, 128, 128};
+  int sms = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  std::string err;
+  BatchState* batch = nullptr;
+  int device = 0;
+};
+
+namespace {
+
+enoao_status fail(enoao_ctx* c, enoao_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_create_error = buf;
+  return st;
+}
+
+#define CU(ctx, call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail((ctx), ENOAO_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr double kInf = std::numeric_limits<double>::infinity();
+
+// ---------------------------------------------------------------- small kernels
+
+// alpha of the current state (Sec. 2: max of |f'(u)| over the mesh; for the
+// Euler equations |u_d| + c per axis) into alpha_acc[slot], plus the
+// non-physical check.
+__global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int ndim, int nv,
+                             double gamma, StepState* st, int slot) {
+  double amax[3] = {0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double rho = U[i];
+    double m2 = 0.0;
+    for (int c = 1; c < nv - 1; ++c) m2 += U[c * ncell + i] * U[c * ncell + i];
+    const double p = (gamma - 1.0) * (U[(nv - 1) * ncell + i] - 0.5 * m2 / rho);
+    if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p)) {
+      atomicOr(&st->err, kErrNonPhys);
+      atomicMin(&st->err_cell, i);
+      continue;
+    }
+    const double cs = sqrt(gamma * p / rho);
+    for (int d = 0; d < ndim; ++d) amax[d] = fmax(amax[d], fabs(U[(1 + d) * ncell + i] / rho) + cs);
+  }
+  __shared__ double red[3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int d = 0; d < 3; ++d) {
+    double v = amax[d];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[d][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int d = 0; d < 3; ++d) {
+      double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (threadIdx.x == 0 && d < ndim && v > 0.0)
+        atomicMax(&st->alpha_acc[slot][d], (unsigned long long)__double_as_longlong(v));
+    }
+  }
+}
+
+struct StepConsts {
+  int system, ndim;
+  double adv_speed;
+  double dx[3];
+};
+
+__device__ void finalize_pending(StepState* st) {
+  if (st->pending) {
+    st->t = st->last ? st->t_end : st->t + st->dt;
+    st->steps += 1;
+    if (st->last) st->done = 1;
+    st->pending = 0;
+  }
+}
+
+// Start of a step: finalise the previous one, fix alpha from U^n and dt from
+// the CFL rule (or the fixed step), shortened to land on t_end.
+__global__ void step_begin_kernel(StepState* st, StepConsts k) {
+  finalize_pending(st);
+  if (st->done || (st->max_steps > 0 && st->steps >= st->max_steps) || st->err) {
+    st->skip = 1;
+    return;
+  }
+  st->skip = 0;
+  const int cur = (int)(st->steps & 1);
+  double s = 0.0;
+  for (int d = 0; d < k.ndim; ++d) {
+    const double a = k.system == ENOAO_EULER
+                         ? __longlong_as_double((long long)st->alpha_acc[cur][d])
+                         : fabs(k.adv_speed);
+    st->alpha[d] = a;
+    s += a / k.dx[d];
+  }
+  st->par = cur ^ 1;
+  for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = 0ull;
+  double dt = st->dt_fixed > 0.0 ? st->dt_fixed : st->cfl / s;
+  st->last = 0;
+  if (st->t + dt >= st->t_end) {
+    dt = st->t_end - st->t;
+    st->last = 1;
+  }
+  st->dt = dt;
+  st->pending = 1;
+}
+
+__global__ void finalize_kernel(StepState* st) { finalize_pending(st); }
+
+// Manual stages (enoao_rk_stage): stage 0 begins a step with the caller's dt.
+__global__ void manual_stage_kernel(StepState* st, StepConsts k, int stage, double dt) {
+  if (stage == 0) {
+    finalize_pending(st);
+    st->skip = 0;
+    const int cur = (int)(st->steps & 1);
+    for (int d = 0; d < k.ndim; ++d)
+      st->alpha[d] = k.system == ENOAO_EULER
+                         ? __longlong_as_double((long long)st->alpha_acc[cur][d])
+                         : fabs(k.adv_speed);
+    st->par = cur ^ 1;
+    for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = 0ull;
+    st->last = 0;
+    st->pending = 0;
+  }
+  st->dt = dt;
+  if (stage == 2) st->pending = 1;  // finalised by the next step start / finalize
+}
+
+// For reconstruct_fluxes: alpha of the current state without starting a step.
+__global__ void alpha_current_kernel(StepState* st, StepConsts k) {
+  finalize_pending(st);
+  const int cur = (int)(st->steps & 1);
+  for (int d = 0; d < k.ndim; ++d)
+    st->alpha[d] = k.system == ENOAO_EULER
+                       ? __longlong_as_double((long long)st->alpha_acc[cur][d])
+                       : fabs(k.adv_speed);
+  st->skip = 0;
+}
+
+__global__ void reset_state_kernel(StepState* st) {
+  StepState z;
+  memset(&z, 0, sizeof z);
+  z.t_end = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+  z.err_cell = 0x7fffffffffffffffll;
+  *st = z;
+}
+
+__global__ void set_run_kernel(StepState* st, double t_end, double cfl, double dt_fixed,
+                               long long max_steps) {
+  st->t_end = t_end;
+  st->cfl = cfl;
+  st->dt_fixed = dt_fixed;
+  st->max_steps = max_steps;
+  st->done = st->t >= t_end ? 1 : 0;
+  st->skip = 0;
+}
+
+// ---------------------------------------------------------------- helpers
+
+StepConsts consts(const enoao_ctx* c) {
+  StepConsts k;
+  k.system = c->cfg.system;
+  k.ndim = c->cfg.ndim;
+  k.adv_speed = c->cfg.adv_speed;
+  for (int d = 0; d < 3; ++d) k.dx[d] = c->dx[d];
+  return k;
+}
+
+bool fp32(const enoao_ctx* c) { return c->cfg.precision == ENOAO_FP32_BULK; }
+
+int halo(int order) { return order / 2 + 2; }
+
+void default_tiles(enoao_ctx* c) {
+  const bool f32 = fp32(c);
+  for (int d = 0; d < c->cfg.ndim; ++d) {
+    if (d == 0) {
+      c->ta[d] = c->cfg.ndim == 1 ? 1 : 2;
+      c->ts[d] = f32 ? 128 : 64;
+      c->block[d] = 128;
+    } else {
+      c->ta[d] = 32;
+      c->ts[d] = f32 ? 32 : 16;
+      c->block[d] = 128;
+    }
+  }
+}
+
+enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
+  if (ta < 1 || ts < 1 || ta * ts > 8192)
+    return fail(c, ENOAO_EINVAL, "tile %dx%d out of range", ta, ts);
+  if (d > 0 && ta != 32 && ta != 16 && ta != 64)
+    return fail(c, ENOAO_EINVAL, "axis %d needs 16, 32 or 64 lines per tile", d);
+  size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), ta, ts);
+  if (smem > 200 * 1024)
+    return fail(c, ENOAO_EINVAL, "tile %dx%d needs %zu bytes of shared memory", ta, ts, smem);
+  return ENOAO_OK;
+}
+
+enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double* u_in,
+                          double* u_out, double* fhat, int8_t* idx) {
+  SweepArgs a;
+  memset(&a, 0, sizeof a);
+  a.u_in = u_in;
+  a.u0 = c->U[0];
+  a.u_out = u_out;
+  a.rhs = c->rhs;
+  a.fhat = fhat;
+  a.idx_out = idx;
+  a.st = c->st;
+  for (int k = 0; k < 3; ++k) {
+    a.n[k] = c->cfg.n[k];
+    a.dx_all[k] = c->dx[k];
+  }
+  a.ncell = c->ncell;
+  a.ndim = c->cfg.ndim;
+  a.dir = d;
+  a.bc = c->cfg.bc[d];
+  a.mode = mode;
+  a.stage = stage;
+  a.ta = c->ta[d];
+  a.ts = c->ts[d];
+  const long long nd = c->cfg.n[d];
+  a.tiles_s = (nd + a.ts - 1) / a.ts;
+  if (d == 0) {
+    const long long rows = c->cfg.n[1] * c->cfg.n[2];
+    a.tiles_a = (rows + a.ta - 1) / a.ta;
+    a.tiles_b = 1;
+  } else {
+    a.tiles_a = (c->cfg.n[0] + a.ta - 1) / a.ta;
+    a.tiles_b = d == 1 ? c->cfg.n[2] : c->cfg.n[1];
+  }
+  a.ntiles = a.tiles_s * a.tiles_a * a.tiles_b;
+  a.inv_dx = 1.0 / c->dx[d];
+  a.gamma = c->cfg.gamma;
+  a.adv_speed = c->cfg.adv_speed;
+  a.delta = c->cfg.delta;
+  a.tie_rel = c->cfg.tie_rel;
+  const size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts);
+  const int block = c->block[d];
+  int per_sm = 1;
+  cudaError_t e;
+  if (fp32(c)) {
+    e = sweep_configure_fp32(c->nv, c->cfg.order, smem);
+    if (e == cudaSuccess) e = sweep_occupancy_fp32(c->nv, c->cfg.order, block, smem, &per_sm);
+  } else {
+    e = sweep_configure_fp64(c->nv, c->cfg.order, smem);
+    if (e == cudaSuccess) e = sweep_occupancy_fp64(c->nv, c->cfg.order, block, smem, &per_sm);
+  }
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "sweep setup: %s", cudaGetErrorString(e));
+  if (per_sm < 1) return fail(c, ENOAO_EINVAL, "sweep tile does not fit on an SM");
+  long long grid = std::min<long long>(a.ntiles, (long long)c->sms * per_sm);
+  if (grid < 1) grid = 1;
+  e = fp32(c) ? sweep_launch_fp32(c->nv, c->cfg.order, a, (int)grid, block, smem, c->s)
+              : sweep_launch_fp64(c->nv, c->cfg.order, a, (int)grid, block, smem, c->s);
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+  return ENOAO_OK;
+}
+
+// One Runge-Kutta stage: every axis, the last one combining.
+enoao_status enqueue_stage(enoao_ctx* c, int stage) {
+  const double* in = c->U[stage];                 // U^n, U1, U2
+  double* out = c->U[stage == 2 ? 0 : stage + 1];  // U1, U2, U^{n+1}
+  const int nd = c->cfg.ndim;
+  for (int d = 0; d < nd; ++d) {
+    int mode;
+    if (d < nd - 1)
+      mode = kModeRhsStore | (d > 0 ? kModeRhsAdd : 0);
+    else
+      mode = kModeCombine | (nd > 1 ? kModeRhsAdd : 0) | (stage == 2 ? kModeAlpha : 0);
+    enoao_status r = launch_sweep(c, d, stage, mode, in, out, nullptr, nullptr);
+    if (r != ENOAO_OK) return r;
+  }
+  return ENOAO_OK;
+}
+
+enoao_status enqueue_step(enoao_ctx* c) {
+  step_begin_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
+  CU(c, cudaGetLastError());
+  for (int s = 0; s < 3; ++s) {
+    enoao_status r = enqueue_stage(c, s);
+    if (r != ENOAO_OK) return r;
+  }
+  return ENOAO_OK;
+}
+
+// Stream ordering against the caller's stream.
+enoao_status enter(enoao_ctx* c) {
+  CU(c, cudaSetDevice(c->device));
+  CU(c, cudaEventRecord(c->ev_a, c->user));
+  CU(c, cudaStreamWaitEvent(c->s, c->ev_a, 0));
+  return ENOAO_OK;
+}
+enoao_status leave(enoao_ctx* c) {
+  CU(c, cudaEventRecord(c->ev_b, c->s));
+  CU(c, cudaStreamWaitEvent(c->user, c->ev_b, 0));
+  return ENOAO_OK;
+}
+
+enoao_status build_graph(enoao_ctx* c, int steps) {
+  if (c->graph && c->graph_steps == steps) return ENOAO_OK;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaGraph_t g;
+  CU(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+  enoao_status r = ENOAO_OK;
+  for (int k = 0; k < steps && r == ENOAO_OK; ++k) r = enqueue_step(c);
+  if (r == ENOAO_OK) {
+    finalize_kernel<<<1, 1, 0, c->s>>>(c->st);
+  }
+  cudaError_t e = cudaStreamEndCapture(c->s, &g);
+  if (r != ENOAO_OK) return r;
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  c->graph_steps = steps;
+  return ENOAO_OK;
+}
+
+int steps_per_graph(const enoao_ctx* c) {
+  // small problems are launch-bound: replay many steps per graph
+  return c->ncell < (1ll << 16) ? 32 : (c->ncell < (1ll << 22) ? 8 : 4);
+}
+
+enoao_status read_host_state(enoao_ctx* c) {
+  CU(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(StepState), cudaMemcpyDeviceToHost, c->s));
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+enoao_status check_err(enoao_ctx* c) {
+  if (c->st_host->err & kErrNonPhys)
+    return fail(c, ENOAO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) at cell %lld",
+                (long long)c->st_host->err_cell);
+  if (c->st_host->err & kErrTimeout) return fail(c, ENOAO_ETIMEOUT, "device wait timed out");
+  return ENOAO_OK;
+}
+
+enoao_status copy_in(enoao_ctx* c, double* dst, const double* src, size_t bytes, int on_device) {
+  CU(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        c->s));
+  return ENOAO_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void enoao_config_default(enoao_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->ndim = 1;
+  cfg->system = ENOAO_EULER;
+  cfg->order = 5;
+  cfg->precision = ENOAO_FP64;
+  for (int d = 0; d < 3; ++d) {
+    cfg->n[d] = 1;
+    cfg->lo[d] = 0.0;
+    cfg->hi[d] = 1.0;
+    cfg->bc[d] = ENOAO_PERIODIC;
+  }
+  cfg->adv_speed = 1.0;
+  cfg->gamma = 1.4;
+  cfg->delta = 1e-5;
+  cfg->tie_rel = 1e-3;
+}
+
+const char* enoao_last_error(const enoao_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+static enoao_status validate(const enoao_config* cfg, bool batched) {
+  if (!cfg) return fail(nullptr, ENOAO_EINVAL, "config is NULL");
+  if (cfg->ndim < 1 || cfg->ndim > 3) return fail(nullptr, ENOAO_EINVAL, "ndim must be 1, 2 or 3");
+  if (cfg->system != ENOAO_EULER && cfg->system != ENOAO_SCALAR_ADVECTION)
+    return fail(nullptr, ENOAO_EINVAL, "unknown system %d", cfg->system);
+  if (cfg->order != 5 && cfg->order != 7) return fail(nullptr, ENOAO_EINVAL, "order must be 5 or 7");
+  if (cfg->precision != ENOAO_FP64 && cfg->precision != ENOAO_FP32_BULK)
+    return fail(nullptr, ENOAO_EINVAL, "unknown precision %d", cfg->precision);
+  if (batched && cfg->ndim != 1)
+    return fail(nullptr, ENOAO_EINVAL, "batched problems must be one-dimensional");
+  for (int d = 0; d < 3; ++d) {
+    if (d < cfg->ndim) {
+      if (!batched && cfg->n[d] < 2 * halo(cfg->order) + 1)
+        return fail(nullptr, ENOAO_EINVAL, "axis %d has %lld cells; at least %d are needed", d,
+                    (long long)cfg->n[d], 2 * halo(cfg->order) + 1);
+      if (!batched && !(cfg->hi[d] > cfg->lo[d]))
+        return fail(nullptr, ENOAO_EINVAL, "axis %d: hi must exceed lo", d);
+      if (cfg->bc[d] != ENOAO_PERIODIC && cfg->bc[d] != ENOAO_TRANSMISSIVE)
+        return fail(nullptr, ENOAO_EINVAL, "axis %d: unknown boundary condition", d);
+    } else if (cfg->n[d] != 1) {
+      return fail(nullptr, ENOAO_EINVAL, "unused axis %d must have n = 1", d);
+    }
+  }
+  if (cfg->system == ENOAO_EULER && !(cfg->gamma > 1.0))
+    return fail(nullptr, ENOAO_EINVAL, "gamma must exceed 1");
+  if (!(cfg->delta >= 0.0)) return fail(nullptr, ENOAO_EINVAL, "delta must be >= 0");
+  if (!(cfg->tie_rel >= 0.0)) return fail(nullptr, ENOAO_EINVAL, "tie_rel must be >= 0");
+  return ENOAO_OK;
+}
+
+static enoao_status create_common(const enoao_config* cfg, void* stream, enoao_ctx** out,
+                                  bool batched) {
+  enoao_ctx* c = new (std::nothrow) enoao_ctx;
+  if (!c) return fail(nullptr, ENOAO_ENOMEM, "host allocation failed");
+  c->cfg = *cfg;
+  c->nv = cfg->system == ENOAO_EULER ? cfg->ndim + 2 : 1;
+  c->user = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->t1);
+  if (e == cudaSuccess) e = cudaMalloc(&c->st, sizeof(StepState));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->st_host, sizeof(StepState));
+  if (e != cudaSuccess) {
+    enoao_status r = fail(nullptr, ENOAO_ECUDA, "context setup: %s", cudaGetErrorString(e));
+    enoao_destroy(c);
+    return r;
+  }
+  if (!batched) {
+    c->ncell = cfg->n[0] * cfg->n[1] * cfg->n[2];
+    for (int d = 0; d < 3; ++d) c->dx[d] = d < cfg->ndim ? (cfg->hi[d] - cfg->lo[d]) / cfg->n[d] : 1.0;
+    const size_t bytes = (size_t)c->nv * c->ncell * sizeof(double);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->U[k], bytes);
+    if (e == cudaSuccess && cfg->ndim > 1)
+      e = cudaMalloc(&c->rhs, (size_t)c->nv * c->ncell * (fp32(c) ? 4 : 8));
+    if (e != cudaSuccess) {
+      enoao_status r = fail(nullptr, e == cudaErrorMemoryAllocation ? ENOAO_ENOMEM : ENOAO_ECUDA,
+                            "device allocation of %zu bytes per state failed: %s", bytes,
+                            cudaGetErrorString(e));
+      enoao_destroy(c);
+      return r;
+    }
+    default_tiles(c);
+  }
+  reset_state_kernel<<<1, 1, 0, c->s>>>(c->st);
+  e = cudaStreamSynchronize(c->s);
+  if (e != cudaSuccess) {
+    enoao_status r = fail(nullptr, ENOAO_ECUDA, "context setup: %s", cudaGetErrorString(e));
+    enoao_destroy(c);
+    return r;
+  }
+  *out = c;
+  return ENOAO_OK;
+}
+
+enoao_status enoao_create(const enoao_config* cfg, void* cuda_stream, enoao_ctx** out) {
+  if (!out) return fail(nullptr, ENOAO_EINVAL, "out is NULL");
+  *out = nullptr;
+  enoao_status r = validate(cfg, false);
+  if (r != ENOAO_OK) return r;
+  return create_common(cfg, cuda_stream, out, false);
+}
+
+enoao_status enoao_batch_create(const enoao_config* proto, int nprob, const int64_t* n,
+                                const double* lo, const double* hi, void* cuda_stream,
+                                enoao_ctx** out) {
+  if (!out) return fail(nullptr, ENOAO_EINVAL, "out is NULL");
+  *out = nullptr;
+  enoao_status r = validate(proto, true);
+  if (r != ENOAO_OK) return r;
+  if (nprob < 1 || !n || !lo || !hi) return fail(nullptr, ENOAO_EINVAL, "empty batch");
+  enoao_ctx* c = nullptr;
+  r = create_common(proto, cuda_stream, &c, true);
+  if (r != ENOAO_OK) return r;
+  r = batch_create(c, proto, nprob, n, lo, hi);
+  if (r != ENOAO_OK) {
+    g_create_error = c->err;
+    enoao_destroy(c);
+    return r;
+  }
+  *out = c;
+  return ENOAO_OK;
+}
+
+void enoao_destroy(enoao_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->s) cudaStreamSynchronize(c->s);
+  if (c->batch) batch_destroy(c->batch);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int k = 0; k < 3; ++k) cudaFree(c->U[k]);
+  cudaFree(c->rhs);
+  cudaFree(c->st);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
+  if (c->t0) cudaEventDestroy(c->t0);
+  if (c->t1) cudaEventDestroy(c->t1);
+  if (c->s) cudaStreamDestroy(c->s);
+  delete c;
+}
+
+enoao_status enoao_init_state(enoao_ctx* c, const double* U, int on_device) {
+  if (!c || !U) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return batch_init_state(c, U, on_device);
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  r = copy_in(c, c->U[0], U, (size_t)c->nv * c->ncell * sizeof(double), on_device);
+  if (r != ENOAO_OK) return r;
+  reset_state_kernel<<<1, 1, 0, c->s>>>(c->st);
+  if (c->cfg.system == ENOAO_EULER) {
+    const int blocks = std::max(1, std::min<int>((int)((c->ncell + 255) / 256), c->sms * 8));
+    alpha_kernel<<<blocks, 256, 0, c->s>>>(c->U[0], c->ncell, c->cfg.ndim, c->nv, c->cfg.gamma,
+                                           c->st, 0);
+  }
+  CU(c, cudaGetLastError());
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  r = read_host_state(c);
+  if (r != ENOAO_OK) return r;
+  return check_err(c);
+}
+
+enoao_status enoao_get_state(enoao_ctx* c, double* U, int on_device) {
+  if (!c || !U) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return batch_get_state(c, U, on_device);
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaMemcpyAsync(U, c->U[0], (size_t)c->nv * c->ncell * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+enoao_status enoao_reconstruct_fluxes(enoao_ctx* c, int dir, double* Fhat, int8_t* idx,
+                                      int on_device) {
+  if (!c || !Fhat) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  if (dir < 0 || dir >= c->cfg.ndim) return fail(c, ENOAO_EINVAL, "dir out of range");
+  const long long nf = c->ncell / c->cfg.n[dir] * (c->cfg.n[dir] + 1);
+  const size_t fbytes = (size_t)c->nv * nf * sizeof(double);
+  const size_t ibytes = (size_t)c->nv * 2 * nf;
+  double* dF = Fhat;
+  int8_t* dI = idx;
+  if (!on_device) {
+    CU(c, cudaMalloc(&dF, fbytes));
+    if (idx) {
+      cudaError_t e = cudaMalloc(&dI, ibytes);
+      if (e != cudaSuccess) {
+        cudaFree(dF);
+        return fail(c, ENOAO_ENOMEM, "scratch allocation failed");
+      }
+    }
+  }
+  enoao_status r = enter(c);
+  if (r == ENOAO_OK) {
+    alpha_current_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
+    r = launch_sweep(c, dir, 0, kModeFlux, c->U[0], nullptr, dF, dI);
+  }
+  if (r == ENOAO_OK && !on_device) {
+    cudaError_t e = cudaMemcpyAsync(Fhat, dF, fbytes, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess && idx) e = cudaMemcpyAsync(idx, dI, ibytes, cudaMemcpyDeviceToHost, c->s);
+    if (e != cudaSuccess) r = fail(c, ENOAO_ECUDA, "copy out: %s", cudaGetErrorString(e));
+  }
+  if (r == ENOAO_OK) r = leave(c);
+  cudaError_t e = cudaStreamSynchronize(c->s);
+  if (!on_device) {
+    cudaFree(dF);
+    if (idx) cudaFree(dI);
+  }
+  if (r != ENOAO_OK) return r;
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "reconstruct_fluxes: %s", cudaGetErrorString(e));
+  return ENOAO_OK;
+}
+
+enoao_status enoao_rk_stage(enoao_ctx* c, int stage, double dt) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  if (stage < 0 || stage > 2) return fail(c, ENOAO_EINVAL, "stage must be 0, 1 or 2");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, ENOAO_EINVAL, "dt must be positive");
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  manual_stage_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c), stage, dt);
+  CU(c, cudaGetLastError());
+  r = enqueue_stage(c, stage);
+  if (r != ENOAO_OK) return r;
+  if (stage == 2) finalize_kernel<<<1, 1, 0, c->s>>>(c->st);
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  if (stage == 2) {
+    r = read_host_state(c);
+    if (r != ENOAO_OK) return r;
+    return check_err(c);
+  }
+  return ENOAO_OK;
+}
+
+static enoao_status run_graph_steps(enoao_ctx* c, double t_end, double cfl, double dt_fixed,
+                                    long long max_steps, bool until_time, bool sync) {
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  r = build_graph(c, steps_per_graph(c));
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(StepState), cudaMemcpyDeviceToHost, c->s));
+  CU(c, cudaStreamSynchronize(c->s));
+  const long long start = c->st_host->steps;
+  const long long limit = max_steps > 0 ? start + max_steps : 0;
+  set_run_kernel<<<1, 1, 0, c->s>>>(c->st, t_end, cfl, dt_fixed, limit);
+  CU(c, cudaGetLastError());
+  if (!until_time) {
+    const long long reps = (max_steps + c->graph_steps - 1) / c->graph_steps;
+    for (long long k = 0; k < reps; ++k) CU(c, cudaGraphLaunch(c->graph, c->s));
+  } else {
+    for (;;) {
+      for (int k = 0; k < 4; ++k) CU(c, cudaGraphLaunch(c->graph, c->s));
+      r = read_host_state(c);
+      if (r != ENOAO_OK) return r;
+      if (c->st_host->done || c->st_host->err) break;
+      if (limit > 0 && c->st_host->steps >= limit) break;
+    }
+  }
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  if (!sync) return ENOAO_OK;
+  r = read_host_state(c);
+  if (r != ENOAO_OK) return r;
+  return check_err(c);
+}
+
+enoao_status enoao_advance(enoao_ctx* c, double t_end, double cfl, double dt_fixed,
+                           int64_t max_steps, double* t_out, int64_t* steps_out) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "use enoao_advance_steps for batched contexts");
+  if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(c, ENOAO_EINVAL, "cfl must be positive");
+  if (!(t_end >= 0.0)) return fail(c, ENOAO_EINVAL, "t_end must be >= 0");
+  enoao_status r = run_graph_steps(c, t_end, cfl, dt_fixed, max_steps, true, true);
+  if (t_out) *t_out = c->st_host->t;
+  if (steps_out) *steps_out = c->st_host->steps;
+  return r;
+}
+
+enoao_status enoao_advance_steps_async(enoao_ctx* c, int64_t nsteps, double cfl) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (!(cfl > 0.0)) return fail(c, ENOAO_EINVAL, "cfl must be positive");
+  if (nsteps < 0) return fail(c, ENOAO_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return ENOAO_OK;
+  if (c->batch) return batch_advance(c, nsteps, cfl, false);
+  return run_graph_steps(c, kInf, cfl, 0.0, nsteps, false, false);
+}
+
+enoao_status enoao_advance_steps(enoao_ctx* c, int64_t nsteps, double cfl) {
+  enoao_status r = enoao_advance_steps_async(c, nsteps, cfl);
+  if (r != ENOAO_OK) return r;
+  return enoao_sync(c);
+}
+
+enoao_status enoao_sync(enoao_ctx* c) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  enoao_status r = read_host_state(c);
+  if (r != ENOAO_OK) return r;
+  return check_err(c);
+}
+
+enoao_status enoao_get_stats(enoao_ctx* c, enoao_stats* out) {
+  if (!c || !out) return fail(c, ENOAO_EINVAL, "NULL argument");
+  enoao_status r = read_host_state(c);
+  if (r != ENOAO_OK) return r;
+  const StepState& h = *c->st_host;
+  out->t = h.pending ? (h.last ? h.t_end : h.t + h.dt) : h.t;
+  out->steps = h.steps + (h.pending ? 1 : 0);
+  for (int d = 0; d < 3; ++d) out->alpha[d] = h.alpha[d];
+  out->dt = h.dt;
+  out->fp64_fallbacks = h.fallbacks;
+  out->decisions = h.decisions;
+  return ENOAO_OK;
+}
+
+int enoao_launches_per_step(const enoao_ctx* c) {
+  if (!c) return 0;
+  if (c->batch) return 0;  // one persistent launch covers every step
+  return 1 + 3 * c->cfg.ndim;
+}
+
+enoao_status enoao_set_tiles(enoao_ctx* c, int dir, int ta, int ts) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (c->batch || dir < 0 || dir >= c->cfg.ndim) return fail(c, ENOAO_EINVAL, "dir out of range");
+  if (ta == 0) ta = c->ta[dir];
+  if (ts == 0) ts = c->ts[dir];
+  enoao_status r = check_tiles(c, dir, ta, ts);
+  if (r != ENOAO_OK) return r;
+  c->ta[dir] = ta;
+  c->ts[dir] = ts;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return ENOAO_OK;
+}
+
+enoao_status enoao_get_tiles(const enoao_ctx* c, int dir, int* ta, int* ts) {
+  if (!c || dir < 0 || dir >= 3) return ENOAO_EINVAL;
+  if (ta) *ta = c->ta[dir];
+  if (ts) *ts = c->ts[dir];
+  return ENOAO_OK;
+}
+
+enoao_status enoao_autotune(enoao_ctx* c) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (c->batch) return ENOAO_OK;  // the batch kernel tunes itself at creation
+  // Save the state; time one stage-0 sweep per candidate on the live state.
+  const size_t bytes = (size_t)c->nv * c->ncell * sizeof(double);
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaMemcpyAsync(c->U[2], c->U[0], bytes, cudaMemcpyDeviceToDevice, c->s));
+  const bool f32 = fp32(c);
+  for (int d = 0; d < c->cfg.ndim; ++d) {
+    std::vector<std::pair<int, int>> cands;
+    if (d == 0) {
+      const int tas[] = {1, 2, 4};
+      const int tss[] = {64, 128, 256};
+      for (int ta : tas)
+        for (int ts : tss)
+          if (c->cfg.ndim > 1 || ta == 1) cands.push_back({ta, ts});
+    } else {
+      const int tas[] = {16, 32, 64};
+      const int tss[] = {8, 16, 32, 64};
+      for (int ta : tas)
+        for (int ts : tss) cands.push_back({ta, ts});
+    }
+    const int best_ta0 = c->ta[d], best_ts0 = c->ts[d];
+    float best = 1e30f;
+    int bta = best_ta0, bts = best_ts0;
+    for (auto& p : cands) {
+      if (check_tiles(c, d, p.first, p.second) != ENOAO_OK) continue;
+      c->ta[d] = p.first;
+      c->ts[d] = p.second;
+      const int mode = kModeCombine;  // stage 0 into U1; the live state U^n is untouched
+      alpha_current_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
+      r = launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr);  // warm-up
+      if (r != ENOAO_OK) continue;
+      CU(c, cudaEventRecord(c->t0, c->s));
+      for (int k = 0; k < 3; ++k) launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr);
+      CU(c, cudaEventRecord(c->t1, c->s));
+      CU(c, cudaEventSynchronize(c->t1));
+      float ms = 0.f;
+      CU(c, cudaEventElapsedTime(&ms, c->t0, c->t1));
+      if (ms < best) {
+        best = ms;
+        bta = p.first;
+        bts = p.second;
+      }
+    }
+    c->ta[d] = bta;
+    c->ts[d] = bts;
+    (void)f32;
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->err.clear();
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+}  // extern "C"

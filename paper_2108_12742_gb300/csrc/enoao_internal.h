@@ -1,0 +1,97 @@
+// Internal declarations shared by the host runtime and the kernels of the
+// ENO-AO library (not part of the public C interface).
+#pragma once
+
+#include <cstdint>
+
+namespace enoao {
+
+constexpr int kMaxNv = 5;
+
+// Device-resident time-stepping state.  Written by the step kernels, read by
+// every sweep launch, so alpha and dt never travel to the host inside a step.
+struct StepState {
+  double alpha[3];          // Lax-Friedrichs alpha per axis of the current step
+  double dt;                // current step size
+  double t;                 // time at the start of the current step
+  double t_end;             // target time of enoao_advance (inf for step counts)
+  double cfl;               // CFL number (dt = cfl / sum alpha_d / dx_d)
+  double dt_fixed;          // > 0: fixed step size instead of the CFL rule
+  long long steps;          // completed steps
+  long long max_steps;      // stop after this many steps (<= 0: none)
+  int skip;                 // 1: the current step is not taken (done / limit)
+  int last;                 // 1: the current step lands on t_end
+  int done;                 // 1: t_end reached
+  int pending;              // 1: a step was begun and is not yet finalised
+  unsigned long long alpha_acc[2][3];  // running max of |u_d| + c (bit patterns);
+                                       // step n reads [n % 2], its last stage fills [par]
+  int par;                  // alpha_acc slot the current step's last stage fills
+  int err;                  // error bits (kErrNonPhys, kErrTimeout)
+  long long err_cell;       // first cell (min index) that raised kErrNonPhys
+  unsigned long long fallbacks;  // FP32-bulk decisions re-done in FP64
+  unsigned long long decisions;  // stencil decisions taken
+};
+
+constexpr int kErrNonPhys = 1;
+constexpr int kErrTimeout = 2;
+
+// Modes of a sweep launch (bit set).
+constexpr int kModeRhsStore = 1;   // write this axis' L(u) into rhs
+constexpr int kModeRhsAdd = 2;     // add the stored rhs of earlier axes
+constexpr int kModeCombine = 4;    // Runge-Kutta combine into u_out
+constexpr int kModeAlpha = 8;      // accumulate alpha of u_out for the next step
+constexpr int kModeFlux = 16;      // write interface fluxes (and choices)
+
+struct SweepArgs {
+  const double* u_in;   // U^(s): stencil source, [nv][N]
+  const double* u0;     // U^n for the Runge-Kutta combine
+  double* u_out;        // combined state
+  void* rhs;            // accumulated L(u) of earlier axes ([nv][N], bulk type)
+  double* fhat;         // kModeFlux: interface fluxes [nv][faces]
+  int8_t* idx_out;      // kModeFlux: choices [nv][2][faces] (nullable)
+  StepState* st;
+  long long n[3];       // cells per axis
+  long long ncell;      // total cells
+  int ndim;
+  int dir;              // swept axis
+  int bc;               // boundary condition along dir
+  int mode;
+  int stage;            // Runge-Kutta stage 0..2
+  int ta, ts;           // tile: lines x faces
+  long long tiles_s;    // tiles along dir
+  long long tiles_a;    // tiles across the line index
+  long long tiles_b;    // tiles along the remaining axis (dir != 0)
+  long long ntiles;
+  double inv_dx;        // 1 / dx along dir
+  double dx_all[3];     // dx per axis (alpha accumulation needs none, kept for checks)
+  double gamma;
+  double adv_speed;
+  double delta;
+  double tie_rel;
+};
+
+// Host-side entry points of the instantiation units (sweep_fp64.cu,
+// sweep_fp32.cu); return cudaError_t values.
+}  // namespace enoao
+#include <cuda_runtime.h>
+namespace enoao {
+cudaError_t sweep_launch_fp64(int nv, int order, const SweepArgs& a, int grid, int block,
+                              size_t smem, cudaStream_t s);
+cudaError_t sweep_launch_fp32(int nv, int order, const SweepArgs& a, int grid, int block,
+                              size_t smem, cudaStream_t s);
+cudaError_t sweep_configure_fp64(int nv, int order, size_t smem);
+cudaError_t sweep_configure_fp32(int nv, int order, size_t smem);
+cudaError_t sweep_occupancy_fp64(int nv, int order, int block, size_t smem, int* per_sm);
+cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm);
+
+// Dynamic shared memory of one sweep block: per extended cell, the split
+// differences (2 nv), the face corrections (nv), the Roe ingredients (nv for
+// the Euler equations) and, in FP32 bulk mode, one magnitude bound.
+inline size_t sweep_smem_bytes(int nv, int order, int fp32, int ta, int ts) {
+  const int G = order / 2 + 2;
+  const size_t cells = (size_t)ta * (size_t)(ts + 2 * G);
+  const int per = 3 * nv + (nv > 1 ? nv : 0) + (fp32 ? 1 : 0);
+  return cells * per * (fp32 ? 4 : 8);
+}
+
+}  // namespace enoao

@@ -1,0 +1,760 @@
+// Fused ENO-AO sweep kernel: one launch performs, for one axis and one
+// Runge-Kutta stage, every step of the spatial operator of Shen's ENO-AO
+// scheme (arXiv 2108.12742) and, on the last axis, the Runge-Kutta combine.
+//
+// Per tile (TA lines x TS cells along the swept axis, plus a halo of G cells
+// on each side, G = 4 for ENO-AO5 and 5 for ENO-AO7):
+//   phase 1  per pair of neighbouring cells: state difference dU (FP64),
+//            flux difference dF in difference form, Lax-Friedrichs split
+//            differences df+- = (dF +- alpha dU)/2 (Sec. 2, Eq. LF_Flux_Split);
+//            per cell: Roe-average ingredients (sqrt rho, velocity, H).
+//   phase 2  per face x_{j+1/2}: Roe average and eigenvectors (Sec. 4),
+//            projection of the window differences onto each characteristic
+//            field, indicators IS = MIN(delta_L, delta_R) as undivided
+//            differences (Eq. New_Smoothness_Indicator, Tables 4-5), stencil
+//            choice by the principle of Sec. 3.2 (ties to the higher
+//            priority as in Appendix A), the chosen Table-1 value written as
+//            f_j + sum_i b_i (f_{i+1} - f_i), the mirrored choice for f^-, and
+//            the back-projection C_{j+1/2} = R (corr^+ + corr^-).
+//   phase 3  per cell: L(u)_j = -(df+_{j-1} + df-_j + C_{j+1/2} - C_{j-1/2})/dx,
+//            which equals -(F_{j+1/2} - F_{j-1/2})/dx of Eq. (1DWENOFD) because
+//            F_{j+1/2} = f+_j + f-_{j+1} + C_{j+1/2}; then either store L(u)
+//            for the next axis or add the earlier axes and apply the
+//            third-order TVD Runge-Kutta combine in FP64, checking the new
+//            state and accumulating the next step's alpha.
+//
+// Writing every quantity as a difference keeps FP32 rounding relative to the
+// local variation |df| instead of |f|; the state and the combine stay FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cstdint>
+
+#include "enoao_internal.h"
+
+namespace enoao {
+
+template <int ORDER>
+struct Geo {
+  static constexpr int G = ORDER / 2 + 2;       // halo cells per side
+  static constexpr int NC = ORDER == 7 ? 9 : 6; // candidates
+  static constexpr int LO = ORDER == 7 ? 0 : 1; // used window differences d[LO..HI]
+  static constexpr int HI = ORDER == 7 ? 7 : 6;
+};
+
+// Chosen value minus the centre value, f^ - f_j = sum_i B[c][i] d[i], for the
+// nine candidates in priority order, with d[i] = f_{j+i-3} - f_{j+i-4}
+// (Table 1 rewritten in first differences).
+__constant__ double kB64[9][8] = {
+    {0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 1.0 / 2, 0, 0, 0},
+    {0, 0, 0, 1.0 / 6, 1.0 / 3, 0, 0, 0},
+    {0, 0, -1.0 / 12, 1.0 / 3, 1.0 / 4, 0, 0, 0},
+    {0, 0, 0, 1.0 / 12, 1.0 / 2, -1.0 / 12, 0, 0},
+    {0, 0, -1.0 / 30, 11.0 / 60, 2.0 / 5, -1.0 / 20, 0, 0},
+    {0, 1.0 / 60, -1.0 / 10, 17.0 / 60, 1.0 / 3, -1.0 / 30, 0, 0},
+    {0, 0, -1.0 / 60, 7.0 / 60, 1.0 / 2, -7.0 / 60, 1.0 / 60, 0},
+    {0, 1.0 / 140, -11.0 / 210, 79.0 / 420, 3.0 / 7, -17.0 / 210, 1.0 / 105, 0},
+};
+__constant__ float kB32[9][8] = {
+    {0, 0, 0, 0, 0, 0, 0, 0},
+    {0, 0, 0, 0, 1.0f / 2, 0, 0, 0},
+    {0, 0, 0, 1.0f / 6, 1.0f / 3, 0, 0, 0},
+    {0, 0, -1.0f / 12, 1.0f / 3, 1.0f / 4, 0, 0, 0},
+    {0, 0, 0, 1.0f / 12, 1.0f / 2, -1.0f / 12, 0, 0},
+    {0, 0, -1.0f / 30, 11.0f / 60, 2.0f / 5, -1.0f / 20, 0, 0},
+    {0, 1.0f / 60, -1.0f / 10, 17.0f / 60, 1.0f / 3, -1.0f / 30, 0, 0},
+    {0, 0, -1.0f / 60, 7.0f / 60, 1.0f / 2, -7.0f / 60, 1.0f / 60, 0},
+    {0, 1.0f / 140, -11.0f / 210, 79.0f / 420, 3.0f / 7, -17.0f / 210, 1.0f / 105, 0},
+};
+
+template <typename R>
+__device__ __forceinline__ R bcoef(int c, int i);
+template <>
+__device__ __forceinline__ double bcoef<double>(int c, int i) { return kB64[c][i]; }
+template <>
+__device__ __forceinline__ float bcoef<float>(int c, int i) { return kB32[c][i]; }
+
+template <typename R>
+__device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+template <typename R>
+__device__ __forceinline__ R rabs(R a) { return a < R(0) ? -a : a; }
+
+// ENO-AO choice on one window of first differences d[LO..HI] (d[i] between
+// offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
+// CHECK is set, 'marginal' reports a decision that rounding of size tol_abs
+// or a relative gap tie_rel could have changed.
+template <int ORDER, typename R, bool CHECK>
+__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R tol_abs,
+                                        int& pick_out, bool& marginal) {
+  using GE = Geo<ORDER>;
+  constexpr int LO = GE::LO, HI = GE::HI, NC = GE::NC;
+  R s2[8], s3[8], s4[8], s5[8], s6[8], s7[8];
+#pragma unroll
+  for (int i = LO; i < HI; ++i) s2[i] = d[i + 1] - d[i];
+#pragma unroll
+  for (int i = LO; i < HI - 1; ++i) s3[i] = s2[i + 1] - s2[i];
+#pragma unroll
+  for (int i = LO; i < HI - 2; ++i) s4[i] = s3[i + 1] - s3[i];
+#pragma unroll
+  for (int i = LO; i < HI - 3; ++i) s5[i] = s4[i + 1] - s4[i];
+  if constexpr (ORDER == 7) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s6[i] = s5[i + 1] - s5[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) s7[i] = s6[i + 1] - s6[i];
+  }
+  R IS[9];
+  IS[0] = rmin(R(0.5) * (rabs(d[3]) + rabs(d[2])), R(0.5) * (rabs(d[4]) + rabs(d[5])));
+  IS[1] = rmin(rabs(s2[3]), rabs(s2[4]));
+  IS[2] = rmin(rabs(s3[2]), rabs(s3[3]));
+  IS[3] = rmin(rabs(s4[1]), rabs(s4[2]));
+  IS[4] = rmin(rabs(s4[2]), rabs(s4[3]));
+  IS[5] = rmin(rabs(s5[1]), rabs(s5[2]));
+  if constexpr (ORDER == 7) {
+    IS[6] = rmin(rabs(s6[0]), rabs(s6[1]));
+    IS[7] = rmin(rabs(s6[1]), rabs(s6[2]));
+    IS[8] = rmin(rabs(s7[0]), rabs(s7[1]));
+  }
+  // Principle 1: the highest-priority candidate with IS <= delta.
+  int pick = -1;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (IS[c] <= delta) pick = c;
+  const bool thr = pick >= 0;
+  // Principle 2: otherwise the smallest IS, equal values to the higher priority.
+  R best = IS[0];
+  if (!thr) {
+    pick = 0;
+#pragma unroll
+    for (int c = 1; c < NC; ++c)
+      if (IS[c] <= best) {
+        best = IS[c];
+        pick = c;
+      }
+  }
+  if constexpr (CHECK) {
+    const R tolT = tie_rel * delta + tol_abs;
+    bool m = false;
+    if (thr) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= tolT);
+    } else {
+      m = (best - delta) <= tolT;
+      const R tolA = tie_rel * best + tol_abs;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m |= (c != pick) && (IS[c] - best <= tolA);
+    }
+    marginal = m;
+  }
+  pick_out = pick;
+  R corr = R(0);
+#pragma unroll
+  for (int i = LO; i <= HI; ++i) corr += bcoef<R>(pick, i) * d[i];
+  return corr;
+}
+
+// Conserved component stored at position c of the permuted state for a sweep
+// along axis dir (momentum along dir first, tangential momenta cyclic).
+template <int NV>
+__device__ __forceinline__ int perm_comp(int c, int dir) {
+  if (NV == 1 || c == 0 || c == NV - 1) return c;
+  constexpr int ND = NV > 2 ? NV - 2 : 1;
+  return 1 + (dir + c - 1) % ND;
+}
+
+// Flux difference F(qb) - F(qa) along the sweep axis, written in differences
+// so that rounding scales with |dq| (Euler: F = [m, m u + p, m_t u, (E+p) u]).
+template <int NV, typename T>
+__device__ __forceinline__ void flux_diff(const T (&qa)[NV], const T (&qb)[NV], const T (&dq)[NV],
+                                          T gm1, T adv, T (&dF)[NV]) {
+  if constexpr (NV == 1) {
+    dF[0] = adv * dq[0];
+  } else {
+    constexpr int NT = NV - 3;  // tangential components
+    const T ia = T(1) / qa[0];
+    const T ib = T(1) / qb[0];
+    const T u = qa[1] * ia;
+    T vt[NT > 0 ? NT : 1], dvt[NT > 0 ? NT : 1];
+    const T du = (dq[1] - u * dq[0]) * ib;
+    T v2 = u * u, vdv = u * du, dv2 = du * du;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      vt[t] = qa[2 + t] * ia;
+      dvt[t] = (dq[2 + t] - vt[t] * dq[0]) * ib;
+      v2 += vt[t] * vt[t];
+      vdv += vt[t] * dvt[t];
+      dv2 += dvt[t] * dvt[t];
+    }
+    const T ke_a = T(0.5) * qa[0] * v2;
+    const T dke = T(0.5) * dq[0] * v2 + qb[0] * (vdv + T(0.5) * dv2);
+    const T pa = gm1 * (qa[NV - 1] - ke_a);
+    const T dp = gm1 * (dq[NV - 1] - dke);
+    const T ub = u + du;
+    dF[0] = dq[1];
+    dF[1] = dq[1] * ub + qa[1] * du + dp;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) dF[2 + t] = dq[2 + t] * ub + qa[2 + t] * du;
+    dF[NV - 1] = (dq[NV - 1] + dp) * ub + (qa[NV - 1] + pa) * du;
+  }
+}
+
+// Physical flux of a permuted state (used only for interface-flux output).
+template <int NV>
+__device__ __forceinline__ void phys_flux(const double (&q)[NV], double gm1, double adv,
+                                          double (&F)[NV]) {
+  if constexpr (NV == 1) {
+    F[0] = adv * q[0];
+  } else {
+    double ke = 0.0;
+#pragma unroll
+    for (int i = 1; i < NV - 1; ++i) ke += q[i] * q[i];
+    ke = 0.5 * ke / q[0];
+    const double p = gm1 * (q[NV - 1] - ke);
+    const double un = q[1] / q[0];
+    F[0] = q[1];
+    F[1] = q[1] * un + p;
+#pragma unroll
+    for (int i = 2; i < NV - 1; ++i) F[i] = q[i] * un;
+    F[NV - 1] = (q[NV - 1] + p) * un;
+  }
+}
+
+// Roe-average ingredients of one cell: sqrt(rho), velocity, total enthalpy.
+template <int NV, typename T>
+__device__ __forceinline__ void roe_prims(const T (&q)[NV], T gm1, T (&pr)[NV]) {
+  if constexpr (NV > 1) {
+    const T ir = T(1) / q[0];
+    T ke = T(0);
+#pragma unroll
+    for (int i = 1; i < NV - 1; ++i) {
+      pr[i] = q[i] * ir;
+      ke += q[i] * pr[i];
+    }
+    const T p = gm1 * (q[NV - 1] - T(0.5) * ke);
+    pr[0] = sqrt(q[0]);
+    pr[NV - 1] = (q[NV - 1] + p) * ir;
+  }
+}
+
+// Eigen-system of the Euler flux Jacobian at the Roe state of a face.
+template <int NV, typename T>
+struct Eigen {
+  T u, vt[NV > 3 ? NV - 3 : 1], H, c, ic, b1, b2, q2;
+};
+
+template <int NV, typename T>
+__device__ __forceinline__ void roe_eigen(const T (&pl)[NV], const T (&prr)[NV], T gm1,
+                                          Eigen<NV, T>& E) {
+  constexpr int NT = NV - 3;
+  const T inv = T(1) / (pl[0] + prr[0]);
+  const T wl = pl[0] * inv, wr = prr[0] * inv;
+  E.u = wl * pl[1] + wr * prr[1];
+  T q2 = E.u * E.u;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    E.vt[t] = wl * pl[2 + t] + wr * prr[2 + t];
+    q2 += E.vt[t] * E.vt[t];
+  }
+  E.H = wl * pl[NV - 1] + wr * prr[NV - 1];
+  E.q2 = q2;
+  const T c2 = gm1 * (E.H - T(0.5) * q2);
+  E.c = sqrt(c2);
+  E.ic = T(1) / E.c;
+  E.b1 = gm1 / c2;
+  E.b2 = T(0.5) * q2 * E.b1;
+}
+
+// Row v of L = R^{-1}; fields ordered (u-c, entropy, shear..., u+c).
+template <int NV, typename T>
+__device__ __forceinline__ void left_row(const Eigen<NV, T>& E, int v, T (&L)[NV]) {
+  constexpr int NT = NV - 3;
+  if (v == 0 || v == NV - 1) {
+    const T s = v == 0 ? T(1) : T(-1);
+    L[0] = T(0.5) * (E.b2 + s * E.u * E.ic);
+    L[1] = T(0.5) * (-E.b1 * E.u - s * E.ic);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) L[2 + t] = T(-0.5) * E.b1 * E.vt[t];
+    L[NV - 1] = T(0.5) * E.b1;
+  } else if (v == 1) {
+    L[0] = T(1) - E.b2;
+    L[1] = E.b1 * E.u;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) L[2 + t] = E.b1 * E.vt[t];
+    L[NV - 1] = -E.b1;
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) L[i] = T(0);
+    L[0] = -E.vt[v - 2];
+    L[v] = T(1);
+  }
+}
+
+// Column v of R.
+template <int NV, typename T>
+__device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[NV]) {
+  constexpr int NT = NV - 3;
+  if (v == 0 || v == NV - 1) {
+    const T s = v == 0 ? T(-1) : T(1);
+    Rc[0] = T(1);
+    Rc[1] = E.u + s * E.c;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Rc[2 + t] = E.vt[t];
+    Rc[NV - 1] = E.H + s * E.u * E.c;
+  } else if (v == 1) {
+    Rc[0] = T(1);
+    Rc[1] = E.u;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Rc[2 + t] = E.vt[t];
+    Rc[NV - 1] = T(0.5) * E.q2;
+  } else {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Rc[i] = T(0);
+    Rc[v] = T(1);
+    Rc[NV - 1] = E.vt[v - 2];
+  }
+}
+
+__device__ __forceinline__ long long bc_map(long long s, long long n, int bc) {
+  if (bc == 0) {
+    long long r = s % n;
+    return r < 0 ? r + n : r;
+  }
+  return s < 0 ? 0 : (s >= n ? n - 1 : s);
+}
+
+// Geometry of one tile: cell(a, s) = base + (a0 + a) * stride_a + s * stride_d.
+struct TileGeo {
+  long long s0, a0, base, stride_a, stride_d, na, nd;
+  long long fbase, fstride_a, fstride_d;  // same for the face array (nd + 1 faces)
+  int nts;                                 // valid cells of the tile along dir
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const SweepArgs& A, long long tile) {
+  TileGeo g;
+  const long long ts_i = tile % A.tiles_s;
+  const long long rest = tile / A.tiles_s;
+  const long long ta_i = rest % A.tiles_a;
+  const long long b = rest / A.tiles_a;
+  const long long n0 = A.n[0], n1 = A.n[1], n2 = A.n[2];
+  g.s0 = ts_i * A.ts;
+  g.a0 = ta_i * A.ta;
+  if (A.dir == 0) {
+    g.nd = n0; g.na = n1 * n2;
+    g.base = 0; g.stride_a = n0; g.stride_d = 1;
+    g.fbase = 0; g.fstride_a = n0 + 1; g.fstride_d = 1;
+  } else if (A.dir == 1) {
+    g.nd = n1; g.na = n0;
+    g.base = b * n1 * n0; g.stride_a = 1; g.stride_d = n0;
+    g.fbase = b * (n1 + 1) * n0; g.fstride_a = 1; g.fstride_d = n0;
+  } else {
+    g.nd = n2; g.na = n0;
+    g.base = b * n0; g.stride_a = 1; g.stride_d = n0 * n1;
+    g.fbase = b * n0; g.fstride_a = 1; g.fstride_d = n0 * n1;
+  }
+  const long long left = g.nd - g.s0;
+  g.nts = (int)(left < A.ts ? left : A.ts);
+  return g;
+}
+
+template <int NV>
+__device__ __forceinline__ void load_state(const double* __restrict__ U, long long ncell,
+                                           long long cell, int dir, double (&q)[NV]) {
+#pragma unroll
+  for (int c = 0; c < NV; ++c) q[c] = __ldg(U + perm_comp<NV>(c, dir) * ncell + cell);
+}
+
+// FP64 re-decision of one FP32 choice: rebuilds the projected window of face
+// j+1/2 (global cell index sj of cell j along the line) from the FP64 state.
+template <int NV, int ORDER>
+__device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& g, int a,
+                                             long long sj, int v, int sign, double alpha) {
+  constexpr int G = Geo<ORDER>::G;
+  const double gm1 = A.gamma - 1.0;
+  double q[2 * G][NV];
+#pragma unroll
+  for (int k = 0; k < 2 * G; ++k) {
+    const long long s = bc_map(sj - G + 1 + k, g.nd, A.bc);
+    const long long cell = g.base + (g.a0 + a) * g.stride_a + s * g.stride_d;
+    double t[NV];
+    load_state<NV>(A.u_in, A.ncell, cell, A.dir, t);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) q[k][c] = t[c];
+  }
+  double L[NV];
+  if constexpr (NV > 1) {
+    double pl[NV], prr[NV], ql[NV], qr[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      ql[c] = q[G - 1][c];
+      qr[c] = q[G][c];
+    }
+    roe_prims<NV, double>(ql, gm1, pl);
+    roe_prims<NV, double>(qr, gm1, prr);
+    Eigen<NV, double> E;
+    roe_eigen<NV, double>(pl, prr, gm1, E);
+    left_row<NV, double>(E, v, L);
+  } else {
+    L[0] = 1.0;
+  }
+  // projected split differences of the window: k -> difference (k, k+1)
+  double w[2 * G - 1];
+#pragma unroll
+  for (int k = 0; k < 2 * G - 1; ++k) {
+    double qa[NV], qb[NV], dq[NV], dF[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      qa[c] = q[k][c];
+      qb[c] = q[k + 1][c];
+      dq[c] = qb[c] - qa[c];
+    }
+    flux_diff<NV, double>(qa, qb, dq, gm1, A.adv_speed, dF);
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+      acc += L[c] * (0.5 * (dF[c] + (sign == 0 ? alpha : -alpha) * dq[c]));
+    w[k] = acc;
+  }
+  // window index k corresponds to difference e = j - G + 1 + k
+  double d[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = 0.0;
+#pragma unroll
+  for (int i = Geo<ORDER>::LO; i <= Geo<ORDER>::HI; ++i)
+    d[i] = sign == 0 ? w[i - 4 + G - 1] : -w[4 - i + G - 1];
+  int pick;
+  bool m;
+  eno_select<ORDER, double, false>(d, A.delta, 0.0, 0.0, pick, m);
+  return pick;
+}
+
+template <int NV>
+struct NPrim {
+  static constexpr int value = NV > 1 ? NV : 0;
+};
+
+template <int NV, int ORDER, typename R>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs A) {
+  using GE = Geo<ORDER>;
+  constexpr int G = GE::G;
+  constexpr bool FP32 = sizeof(R) == 4;
+  constexpr int NP = NPrim<NV>::value;
+  StepState* st = A.st;
+  if (st->skip) return;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TA = A.ta, TS = A.ts;
+  const int SE = TS + 2 * G;
+  const int cells = TA * SE;
+  R* dfp = reinterpret_cast<R*>(smem_raw);
+  R* dfm = dfp + NV * cells;
+  R* Cf = dfm + NV * cells;
+  R* prim = Cf + NV * cells;
+  R* mx = prim + NP * cells;  // FP32 only
+
+  const int dir = A.dir;
+  const bool sfast = dir == 0;
+  const double alpha_d = st->alpha[dir];
+  const R alpha = (R)alpha_d;
+  const R gm1 = (R)(A.gamma - 1.0);
+  const R adv = (R)A.adv_speed;
+  const R delta = (R)A.delta;
+  const R tie_rel = (R)A.tie_rel;
+  const double dt = st->dt;
+  const int mode = A.mode;
+  const double inv_dx = A.inv_dx;
+
+  double amax[3] = {0.0, 0.0, 0.0};
+  unsigned long long nfall = 0;
+
+  auto sidx = [&](int a, int e) { return sfast ? a * SE + e : e * TA + a; };
+
+  for (long long tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    const TileGeo g = tile_geo(A, tile);
+    const int nts = g.nts;
+    const int sext = nts + 2 * G;  // extended cells in use
+
+    // ---------------- phase 1: split differences and Roe ingredients
+    {
+      const int cnt = sext;
+      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+        const int e = sfast ? it % cnt : it / TA;
+        const int a = sfast ? it / cnt : it % TA;
+        if (g.a0 + a >= g.na) continue;
+        const long long la = g.base + (g.a0 + a) * g.stride_a;
+        const long long sa = bc_map(g.s0 - G + e, g.nd, A.bc);
+        double qa64[NV];
+        load_state<NV>(A.u_in, A.ncell, la + sa * g.stride_d, dir, qa64);
+        R qa[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) qa[c] = (R)qa64[c];
+        const int si = sidx(a, e);
+        if constexpr (NP > 0) {
+          if (e >= G - 1 && e <= G + nts) {
+            R pr[NV];
+            roe_prims<NV, R>(qa, gm1, pr);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) prim[c * cells + si] = pr[c];
+          }
+        }
+        if (e + 1 < cnt) {
+          const long long sb = bc_map(g.s0 - G + e + 1, g.nd, A.bc);
+          double qb64[NV];
+          load_state<NV>(A.u_in, A.ncell, la + sb * g.stride_d, dir, qb64);
+          R qb[NV], dq[NV], dF[NV];
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            qb[c] = (R)qb64[c];
+            dq[c] = (R)(qb64[c] - qa64[c]);
+          }
+          flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
+          R m = R(0);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            const R p = R(0.5) * (dF[c] + alpha * dq[c]);
+            const R n = R(0.5) * (dF[c] - alpha * dq[c]);
+            dfp[c * cells + si] = p;
+            dfm[c * cells + si] = n;
+            if constexpr (FP32) m = fmaxf(m, fmaxf(fabsf(p), fabsf(n)));
+          }
+          if constexpr (FP32) mx[si] = m;
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase 2: per face choice and back-projection
+    {
+      const int cnt = nts + 1;
+      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+        const int f = sfast ? it % cnt : it / TA;
+        const int a = sfast ? it / cnt : it % TA;
+        if (g.a0 + a >= g.na) continue;
+        const int j = G - 1 + f;  // face j+1/2 in extended cells
+        Eigen<NV, R> E;
+        if constexpr (NV > 1) {
+          R pl[NV], prr[NV];
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            pl[c] = prim[c * cells + sidx(a, j)];
+            prr[c] = prim[c * cells + sidx(a, j + 1)];
+          }
+          roe_eigen<NV, R>(pl, prr, gm1, E);
+        }
+        R M = R(0);
+        if constexpr (FP32) {
+#pragma unroll
+          for (int e = j - G + 1; e <= j + G - 1; ++e) M = fmaxf(M, mx[sidx(a, e)]);
+        }
+        const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
+        const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
+        R C[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) C[c] = R(0);
+#pragma unroll 1
+        for (int v = 0; v < NV; ++v) {
+          R L[NV];
+          if constexpr (NV > 1) {
+            left_row<NV, R>(E, v, L);
+          } else {
+            L[0] = R(1);
+          }
+          R dp[8], dm[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) dp[i] = dm[i] = R(0);
+#pragma unroll
+          for (int i = GE::LO; i <= GE::HI; ++i) {
+            const int ep = sidx(a, j - 4 + i);
+            const int em = sidx(a, j + 4 - i);
+            R sp = R(0), sm = R(0);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+              sp += L[c] * dfp[c * cells + ep];
+              sm += L[c] * dfm[c * cells + em];
+            }
+            dp[i] = sp;
+            dm[i] = -sm;
+          }
+          R tol = R(0);
+          if constexpr (FP32) {
+            R ln = R(0);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
+            tol = R(1 << ORDER) * FLT_EPSILON * ln * M;
+          }
+          int ip, im;
+          bool mp = false, mm = false;
+          R cp = eno_select<ORDER, R, FP32>(dp, delta, tie_rel, tol, ip, mp);
+          R cm = eno_select<ORDER, R, FP32>(dm, delta, tie_rel, tol, im, mm);
+          if constexpr (FP32) {
+            if (mp || mm) {
+              const long long sj = g.s0 + f - 1;
+              if (mp) {
+                ip = redo_choice_fp64<NV, ORDER>(A, g, a, sj, v, 0, alpha_d);
+                cp = R(0);
+#pragma unroll
+                for (int i = GE::LO; i <= GE::HI; ++i) cp += bcoef<R>(ip, i) * dp[i];
+                ++nfall;
+              }
+              if (mm) {
+                im = redo_choice_fp64<NV, ORDER>(A, g, a, sj, v, 1, alpha_d);
+                cm = R(0);
+#pragma unroll
+                for (int i = GE::LO; i <= GE::HI; ++i) cm += bcoef<R>(im, i) * dm[i];
+                ++nfall;
+              }
+            }
+          }
+          if ((mode & kModeFlux) && A.idx_out && own) {
+            const long long nf = A.ncell / g.nd * (g.nd + 1);
+            const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+            A.idx_out[(v * 2 + 0) * nf + fc] = (int8_t)ip;
+            A.idx_out[(v * 2 + 1) * nf + fc] = (int8_t)im;
+          }
+          const R cv = cp + cm;
+          if constexpr (NV > 1) {
+            R Rc[NV];
+            right_col<NV, R>(E, v, Rc);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) C[c] += Rc[c] * cv;
+          } else {
+            C[0] += cv;
+          }
+        }
+        const int sj = sidx(a, j);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) Cf[c * cells + sj] = C[c];
+      }
+    }
+    __syncthreads();
+
+    // ---------------- phase 3: flux difference and Runge-Kutta combine
+    if (mode & kModeFlux) {
+      const int cnt = nts + 1;
+      const long long nf = A.ncell / g.nd * (g.nd + 1);
+      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+        const int f = sfast ? it % cnt : it / TA;
+        const int a = sfast ? it / cnt : it % TA;
+        if (g.a0 + a >= g.na) continue;
+        const long long gface = g.s0 + f;
+        if (!((gface <= g.nd) && (f < A.ts || gface == g.nd))) continue;
+        const int j = G - 1 + f;
+        const long long la = g.base + (g.a0 + a) * g.stride_a;
+        double ql[NV], qr[NV], Fl[NV], Fr[NV];
+        load_state<NV>(A.u_in, A.ncell, la + bc_map(gface - 1, g.nd, A.bc) * g.stride_d, dir, ql);
+        load_state<NV>(A.u_in, A.ncell, la + bc_map(gface, g.nd, A.bc) * g.stride_d, dir, qr);
+        phys_flux<NV>(ql, A.gamma - 1.0, A.adv_speed, Fl);
+        phys_flux<NV>(qr, A.gamma - 1.0, A.adv_speed, Fr);
+        const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
+          const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
+          A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + (double)Cf[c * cells + sidx(a, j)];
+        }
+      }
+    } else {
+      const int cnt = nts;
+      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+        const int t = sfast ? it % cnt : it / TA;
+        const int a = sfast ? it / cnt : it % TA;
+        if (g.a0 + a >= g.na) continue;
+        const int e = G + t;
+        const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
+        R r[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const R s = dfp[c * cells + sidx(a, e - 1)] + dfm[c * cells + sidx(a, e)] +
+                      (Cf[c * cells + sidx(a, e)] - Cf[c * cells + sidx(a, e - 1)]);
+          r[c] = -s * (R)inv_dx;
+        }
+        if (!(mode & kModeCombine)) {
+          R* rb = reinterpret_cast<R*>(A.rhs);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            const long long k = perm_comp<NV>(c, dir) * A.ncell + cell;
+            rb[k] = (mode & kModeRhsAdd) ? rb[k] + r[c] : r[c];
+          }
+          continue;
+        }
+        double unew[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const long long k = perm_comp<NV>(c, dir) * A.ncell + cell;
+          double Lk;
+          if (mode & kModeRhsAdd) {
+            Lk = (double)(reinterpret_cast<const R*>(A.rhs)[k]) + (double)r[c];
+          } else {
+            Lk = (double)r[c];
+          }
+          const double ui = A.u_in[k];
+          double un;
+          if (A.stage == 0) {
+            un = ui + dt * Lk;
+          } else if (A.stage == 1) {
+            un = 0.75 * A.u0[k] + 0.25 * (ui + dt * Lk);
+          } else {
+            un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
+          }
+          A.u_out[k] = un;
+          unew[perm_comp<NV>(c, dir)] = un;  // back in conserved order
+        }
+        if constexpr (NV > 1) {
+          // non-physical check and next-step alpha on the new state
+          const double rho = unew[0];
+          double m2 = 0.0;
+#pragma unroll
+          for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
+          const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 / rho);
+          const bool ok = rho > 0.0 && p > 0.0 && isfinite(p);
+          if (!ok) {
+            atomicOr(&st->err, kErrNonPhys);
+            atomicMin(&st->err_cell, cell);
+          } else if ((mode & kModeAlpha) && A.stage == 2) {
+            const double cs = sqrt(A.gamma * p / rho);
+#pragma unroll
+            for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
+          }
+        } else {
+          if (!isfinite(unew[0])) {
+            atomicOr(&st->err, kErrNonPhys);
+            atomicMin(&st->err_cell, cell);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if constexpr (FP32) {
+    if (nfall) atomicAdd(&st->fallbacks, nfall);
+  }
+  if (NV > 1 && (mode & kModeAlpha) && A.stage == 2) {
+    // block max of |u_d| + c, then one atomic per block and axis
+    __shared__ double red[3][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double v = amax[d];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) red[d][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0 && d < A.ndim && v > 0.0)
+          atomicMax(&st->alpha_acc[st->par][d], (unsigned long long)__double_as_longlong(v));
+      }
+    }
+  }
+}
+
+}  // namespace enoao

@@ -1,0 +1,229 @@
+"""Parity of the CUDA path (through the C interface) with the FP64 oracle.
+
+FP64 bulk: per-step max-norm relative error <= 1e-12 from identical input
+states; stencil choices identical except where the oracle's deciding
+comparison is a near-tie (gap <= 1e-13 relative to the indicator terms).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2108_12742_gb300 as eno
+from paper_2108_12742_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TIE = 1e-13
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_12742_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _smooth_adv(n):
+    return inputs.advection_random(n, seed=n, smooth=True)
+
+
+CASES = {
+    # name: (shape, lo, hi, system, order, bc, initial state, adv_speed)
+    "adv1d-sine-ao5": ((200,), (-1.0,), (1.0,), eno.SCALAR_ADVECTION, 5, eno.PERIODIC,
+                       lambda: inputs.advection_sine(200), 1.0),
+    "adv1d-square-ao7": ((97,), (-1.0,), (1.0,), eno.SCALAR_ADVECTION, 7, eno.PERIODIC,
+                         lambda: inputs.advection_square(97, seed=1), 1.0),
+    "adv1d-noise-ao5-neg": ((61,), (-1.0,), (1.0,), eno.SCALAR_ADVECTION, 5, eno.PERIODIC,
+                            lambda: inputs.advection_random(61, seed=2), -1.3),
+    "adv1d-min-ao7": ((11,), (-1.0,), (1.0,), eno.SCALAR_ADVECTION, 7, eno.TRANSMISSIVE,
+                      lambda: inputs.advection_random(11, seed=3), 0.7),
+    "euler1d-riemann-ao5": ((2000,), (0.0,), (1.0,), eno.EULER, 5, eno.TRANSMISSIVE,
+                            lambda: inputs.euler1d_riemann(2000, seed=1), 0.0),
+    "euler1d-riemann-ao7": ((333,), (0.0,), (1.0,), eno.EULER, 7, eno.TRANSMISSIVE,
+                            lambda: inputs.euler1d_riemann(333, seed=5), 0.0),
+    "euler1d-periodic-ao5": ((150,), (0.0,), (1.0,), eno.EULER, 5, eno.PERIODIC,
+                             lambda: inputs.euler1d_riemann(150, seed=6), 0.0),
+    "euler2d-quad-ao5": ((70, 45), (0.0, 0.0), (1.0, 1.0), eno.EULER, 5, eno.TRANSMISSIVE,
+                         lambda: inputs.euler2d_quadrants(70, 45, seed=1), 0.0),
+    "euler2d-random-ao7": ((40, 37), (0.0, 0.0), (1.0, 1.0), eno.EULER, 7, eno.PERIODIC,
+                           lambda: inputs.euler2d_random(40, 37, seed=2), 0.0),
+    "adv2d-ao5": ((33, 29), (0.0, 0.0), (1.0, 1.0), eno.SCALAR_ADVECTION, 5, eno.PERIODIC,
+                  lambda: inputs.advection_random(33 * 29, seed=4).reshape(1, 1, 29, 33), 0.8),
+    "euler3d-blast-ao7": ((20, 18, 16), (0.0,) * 3, (1.0,) * 3, eno.EULER, 7, eno.PERIODIC,
+                          lambda: inputs.euler3d_blast(20, seed=3)[:, :16, :18, :20].copy(), 0.0),
+    "euler3d-blast-ao5": ((19, 17, 13), (0.0,) * 3, (1.0,) * 3, eno.EULER, 5, eno.TRANSMISSIVE,
+                          lambda: inputs.euler3d_blast(19, seed=4)[:, :13, :17, :19].copy(), 0.0),
+}
+
+
+def _make(name, precision=eno.FP64):
+    shape, lo, hi, system, order, bc, init, a = CASES[name]
+    s = eno.Solver(shape, lo, hi, system=system, order=order, bc=bc, adv_speed=a or 1.0,
+                   precision=precision)
+    P = oracle.make_problem(shape, lo, hi, system=system, order=order, bc=bc, adv_speed=a or 1.0)
+    return s, P, np.ascontiguousarray(init())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fluxes_and_choices_match_oracle(name):
+    s, P, U0 = _make(name)
+    with s:
+        s.init_state(U0)
+        for d in range(len(s.shape)):
+            F, idx = s.reconstruct_fluxes(d, want_idx=True)
+            Fo, io, gap = oracle.fluxes(P, U0, d, want_idx=True)
+            differ = idx != io
+            assert not (differ & (gap > TIE)).any(), \
+                f"{differ.sum()} choices differ away from near-ties (axis {d})"
+            face_ok = ~differ.any(axis=(0, 1))
+            assert relerr(F[:, face_ok], Fo[:, face_ok]) <= TOL64, d
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_one_step_matches_oracle(name):
+    s, P, U0 = _make(name)
+    with s:
+        s.init_state(U0)
+        U = U0
+        for k in range(3):   # per step, from identical input states
+            s.init_state(U)
+            s.advance(1e9, cfl=0.5, max_steps=1)
+            st = s.stats()
+            got = s.get_state()
+            ref = oracle.step(P, U, st.dt)
+            assert relerr(got, ref) <= TOL64, (k, relerr(got, ref))
+            a = oracle.alpha(P, U)
+            for d in range(len(s.shape)):
+                assert st.alpha[d] == pytest.approx(a[d], rel=1e-14)
+            U = got
+
+
+def test_rk_stages_equal_one_advance_step():
+    s, P, U0 = _make("euler2d-quad-ao5")
+    with s:
+        s.init_state(U0)
+        s.advance(1e9, cfl=0.5, max_steps=1)
+        dt = s.stats().dt
+        a = s.get_state()
+        s.init_state(U0)
+        for k in range(3):
+            s.rk_stage(k, dt)
+        b = s.get_state()
+        st = s.stats()
+    assert np.array_equal(a, b)
+    assert st.steps == 1 and st.t == dt
+
+
+def test_device_and_host_buffers_agree():
+    import torch
+    s, P, U0 = _make("euler1d-riemann-ao7")
+    with s:
+        s.init_state(torch.from_numpy(U0).cuda())
+        s.advance(1e9, cfl=0.5, max_steps=5)
+        dev = torch.empty(U0.shape, dtype=torch.float64, device="cuda")
+        s.get_state(dev)
+        host = s.get_state()
+        F = torch.empty(s.face_shape(0), dtype=torch.float64, device="cuda")
+        idx = torch.empty((3, 2) + s.face_shape(0)[1:], dtype=torch.int8, device="cuda")
+        s.reconstruct_fluxes(0, want_idx=True, out=F, idx_out=idx)
+        Fh, ih = s.reconstruct_fluxes(0, want_idx=True)
+    assert np.array_equal(dev.cpu().numpy(), host)
+    assert np.array_equal(F.cpu().numpy(), Fh) and np.array_equal(idx.cpu().numpy(), ih)
+
+
+def test_advection_full_run_matches_oracle_and_paper_order():
+    # the periodic sine workload to t = 2 (400 steps at CFL 0.5): drift over the
+    # whole run stays at round-off, and the error against the exact solution
+    # equals the oracle's
+    s, P, U0 = _make("adv1d-sine-ao5")
+    with s:
+        s.init_state(U0)
+        t, k = s.advance(2.0, cfl=0.5)
+        got = s.get_state()
+    ref, tr, kr = oracle.advance(P, U0, 2.0, cfl=0.5)
+    assert (t, k) == (tr, kr) == (2.0, 400)
+    assert relerr(got, ref) <= 1e-11
+    assert abs(np.abs(got - U0).mean() - np.abs(ref - U0).mean()) <= 1e-14
+
+
+def test_table6_ao7_row_on_gpu():
+    # Sec. 4.1 convergence workload at mesh size 1/30 with dt = dx^(7/3)
+    n = 60
+    with eno.Solver((n,), (-1.0,), (1.0,), system=eno.SCALAR_ADVECTION, order=7,
+                    bc=eno.PERIODIC) as s:
+        U0 = inputs.advection_sine(n)
+        s.init_state(U0)
+        t, _ = s.advance(2.0, dt_fixed=(2.0 / n) ** (7 / 3))
+        e = np.abs(s.get_state() - U0)
+    assert t == 2.0
+    assert e.mean() == pytest.approx(2.17e-9, rel=0.05)
+    assert e.max() == pytest.approx(3.46e-9, rel=0.05)
+
+
+@pytest.mark.parametrize("name", ["euler1d-riemann-ao5", "euler2d-quad-ao5"])
+def test_constant_state_gives_identical_fluxes(name):
+    s, P, U0 = _make(name)
+    const = np.broadcast_to(U0[:, :1, :1, :1], U0.shape).copy()
+    with s:
+        s.init_state(const)
+        for d in range(len(s.shape)):
+            F, _ = s.reconstruct_fluxes(d)
+            assert (F == F.reshape(F.shape[0], -1)[:, :1].reshape(-1, 1, 1, 1)).all()
+        s.advance(1e9, cfl=0.5, max_steps=2)
+        got = s.get_state()
+    assert np.abs(got - const).max() <= 8 * np.spacing(np.abs(const).max())
+
+
+def test_full_c2_run_per_step_samples():
+    # the 1D Euler workload at its full size (N = 2000, t_end = 0.2): run on the
+    # GPU, and at sampled steps re-do that step in the oracle from the GPU state
+    s, P, U0 = _make("euler1d-riemann-ao5")
+    with s:
+        s.init_state(U0)
+        U = U0
+        total = 0
+        for chunk in (1, 50, 200, 400):
+            s.advance(0.2, cfl=0.5, max_steps=chunk)
+            U = s.get_state()
+            s.advance(0.2, cfl=0.5, max_steps=1)
+            st = s.stats()
+            got = s.get_state()
+            ref = oracle.step(P, U, st.dt)
+            assert relerr(got, ref) <= TOL64, (st.steps, relerr(got, ref))
+            total = st.steps
+        t, k = s.advance(0.2, cfl=0.5)
+    assert t == 0.2 and k > total
+
+
+def test_errors_come_back_as_status_codes():
+    with pytest.raises(eno.EnoaoError) as e:
+        eno.Solver((8,), (0.0,), (1.0,), order=7)
+    assert e.value.status == 1 and "cells" in str(e.value)
+    with pytest.raises(eno.EnoaoError) as e:
+        eno.Solver((64,), (0.0,), (1.0,), order=6)
+    assert e.value.status == 1
+    with pytest.raises(eno.EnoaoError):
+        eno.Solver((0,), (0.0,), (1.0,))
+    with eno.Solver((64,), (0.0,), (1.0,)) as s:
+        bad = inputs.euler1d_riemann(64, seed=1)
+        bad[0, 0, 0, 10] = -1.0
+        with pytest.raises(eno.EnoaoError) as e:
+            s.init_state(bad)
+        assert e.value.status == 4 and "cell 10" in str(e.value)
+        good = inputs.euler1d_riemann(64, seed=1)
+        s.init_state(good)
+        s.advance_steps(0)
+        with pytest.raises(eno.EnoaoError):
+            s.rk_stage(3, 0.1)
+        with pytest.raises(eno.EnoaoError):
+            s.reconstruct_fluxes(1)
