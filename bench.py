@@ -1,0 +1,327 @@
+"""Benchmark: ENO-AO cell-stage updates per second on the 2D Euler workload.
+
+Workload (seeded, synthetic): 2D Euler, gamma 1.4, 4096 x 4096 cells on
+[0,1]^2, transmissive boundaries, four-quadrant Riemann data (rho, p ~
+U[0.1,1.5], u, v ~ U[-1,1] per quadrant, split point ~ U[0.4,0.6]^2),
+dimension-by-dimension characteristic ENO-AO5, third-order TVD Runge-Kutta,
+CFL 0.5.  A step is one Runge-Kutta step (three stages, both axes) over the
+whole grid.  The metric compares the FP32-bulk path (reconstruction in FP32,
+state and Runge-Kutta accumulation in FP64) with the all-FP64 path; the
+line's value is the FP32-bulk throughput, the FP64 throughput and the L1
+difference of the two states after the timed steps ride along.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+With --impl reference the reference arm is the FP64 C oracle on the host
+cores, one step per iteration on a bounded sub-block of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS = 4096
+CFL = 0.5
+SEED = 1
+METRIC = "ENO-AO cell-stage updates/s (FP64 vs FP32-mixed) + L1 err vs FP64 oracle"
+WORKLOAD = "euler2d-4096x4096-quadrant-riemann-ao5"
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_state():
+    from paper_2108_12742_gb300 import inputs
+    return inputs.euler2d_quadrants(N_CELLS, N_CELLS, seed=SEED)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_sample(U0, sub, nthreads=0):
+    """One oracle step on a sub x sub block of the workload (the full grid's
+    alpha and dt), returning (cell-stage updates/s, seconds, threads)."""
+    import oracle
+    blk = np.ascontiguousarray(U0[:, :, :sub, :sub])
+    P = oracle.make_problem((sub, sub), (0.0, 0.0), (sub / N_CELLS, sub / N_CELLS),
+                            system=oracle.EULER, order=5, bc=oracle.TRANSMISSIVE,
+                            nthreads=nthreads)
+    alpha = oracle.alpha(P, U0)
+    dx = 1.0 / N_CELLS
+    dt = CFL / (alpha[0] / dx + alpha[1] / dx)
+    t0 = time.perf_counter()
+    oracle.step_alpha(P, blk, dt, alpha)
+    sec = time.perf_counter() - t0
+    threads = nthreads if nthreads > 0 else (os.cpu_count() or 1)
+    return sub * sub * 3 / sec, sec, threads
+
+
+def run_reference(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    U0 = workload_state()
+    sub = 512
+    for _ in range(args.warmup):
+        cpu_sample(U0, sub)
+    secs = []
+    rate = threads = None
+    for _ in range(args.steps):
+        rate, sec, threads = cpu_sample(U0, sub)
+        secs.append(sec)
+    total = sum(secs)
+    value = sub * sub * 3 * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-stage updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": N_CELLS * N_CELLS, "order": 5, "cfl": CFL,
+                   "sample": f"one step of a {sub}x{sub} sub-block per iteration",
+                   "l2": "inputs larger than L2 not applicable (host run)"},
+        "cpu_baseline": {"value": value, "unit": "cell-stage updates/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"one RK3 step of a {sub}x{sub} block of the 4096^2 workload"},
+        "e2e": {"value": value, "unit": "cell-stage updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2108_12742_gb300 as eno
+
+    ws, rank, local = _dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    U0 = workload_state()
+    nbytes = U0.nbytes
+    stream = torch.cuda.current_stream()
+    dev_U0 = torch.from_numpy(U0).cuda()
+
+    def make(precision):
+        s = eno.Solver((N_CELLS, N_CELLS), (0.0, 0.0), (1.0, 1.0), stream=stream,
+                       system=eno.EULER, order=5, bc=eno.TRANSMISSIVE, precision=precision)
+        s.init_state(dev_U0)
+        if not args.no_autotune:
+            s.autotune()
+        s.init_state(dev_U0)
+        return s
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(s, k):
+        s.advance_steps(args.warmup, CFL)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.advance_steps_async(k, CFL)
+        e1.record(stream)
+        s.sync()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    cells = N_CELLS * N_CELLS
+    # ---- FP32-bulk (the line's value)
+    s32 = make(eno.FP32_BULK)
+    clk = ClockSampler(local)
+    clk.start()
+    ms32 = timed(s32, args.steps)
+    clocks = clk.stop()
+    st32 = s32.stats()
+    # dominant kernel: the last-axis sweep (combine), timed alone on its stream
+    k_ms32 = [s32.time_sweep(d, 5) for d in range(2)]
+    # ---- FP64
+    k64 = max(1, min(args.steps, args.fp64_steps))
+    s64 = make(eno.FP64)
+    ms64 = timed(s64, k64)
+    k_ms64 = [s64.time_sweep(d, 2) for d in range(2)]
+    # ---- L1 difference FP32-bulk vs FP64 after the same number of steps
+    s32.init_state(dev_U0)
+    s64.init_state(dev_U0)
+    kcmp = k64
+    s32.advance_steps(kcmp, CFL)
+    s64.advance_steps(kcmp, CFL)
+    a = torch.empty_like(dev_U0)
+    b = torch.empty_like(dev_U0)
+    s32.get_state(a)
+    s64.get_state(b)
+    diff = (a - b).abs()
+    l1 = [float(diff[v].mean() / b[v].abs().mean()) for v in range(4)]
+    linf = [float(diff[v].max() / b[v].abs().max()) for v in range(4)]
+    decisions = 2 * 4 * 3 * 2 * cells  # fields x signs x stages x axes per step (faces ~ cells)
+    fallback_rate = st32.fp64_fallbacks / max(1, decisions * (st32.steps))
+
+    # ---- end to end through the public API with host buffers (FP32-bulk)
+    host_in = torch.from_numpy(U0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ke2e = max(1, min(args.steps, 10))
+    s32.init_state(host_in.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke2e):
+        s32.init_state(host_in.numpy())
+        s32.advance_steps(1, CFL)
+        s32.get_state(host_out.numpy())
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    e2e_value = cells * 3 * ke2e / e2e_sec * ws
+
+    value = cells * 3 * args.steps / (ms32 / 1e3) * ws
+    value64 = cells * 3 * k64 / (ms64 / 1e3) * ws
+
+    # roofline of the dominant FP32-bulk kernel: the y-axis sweep with the
+    # Runge-Kutta combine.  Algorithmic bytes per cell of that launch: read
+    # U^(s) (32 B) and the stored x-axis L(u) (16 B), write U^(s+1) (32 B);
+    # stage 0 reads U^n as U^(s) (later stages add 32 B for U^n; the timed
+    # launch is stage 0).
+    peaks, peak_kind = measured_peaks()
+    dom = 1
+    bytes_per_cell = 32 + 16 + 32
+    achieved = bytes_per_cell * cells / (k_ms32[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "sweep_kernel<4,5,float> axis y (stage 0, combine)",
+                "peak_kind": peak_kind}
+
+    launches = (s32.launches_per_step() * args.steps) if rank == 0 else 0
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, sec, threads = cpu_sample(U0, args.cpu_sub)
+        cpu = {"value": rate, "unit": "cell-stage updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"one RK3 step of a {args.cpu_sub}x{args.cpu_sub} block of the "
+                         f"4096^2 workload ({sec:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-stage updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-bulk/f64-state", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "order": 5, "cfl": CFL,
+                       "seed": SEED, "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (537 MB state per array)",
+                       "tiles": {d: s32.get_tiles(d) for d in range(2)}},
+            "fp64": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
+                     "kernel_ms": k_ms64},
+            "fp32_bulk_speedup_vs_fp64": value / value64,
+            "l1_rel_fp32_bulk_vs_fp64": l1, "linf_rel_fp32_bulk_vs_fp64": linf,
+            "compare_steps": kcmp, "fp64_fallback_rate": fallback_rate,
+            "kernel_ms_fp32_bulk": k_ms32,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "cell-stage updates/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line))
+    for s in (s32, s64):
+        s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-sub", type=int, default=768)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

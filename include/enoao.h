@@ -180,6 +180,13 @@ int enoao_launches_per_step(const enoao_ctx *ctx);
 enoao_status enoao_set_tiles(enoao_ctx *ctx, int dir, int ta, int ts);
 enoao_status enoao_get_tiles(const enoao_ctx *ctx, int dir, int *ta, int *ts);
 
+/* Measurement helper: launches the sweep kernel of axis dir for Runge-Kutta
+ * stage 0 on the current state nrep times back to back on the library's
+ * stream, timed with CUDA events recorded on that stream, and returns the
+ * mean duration of one launch in milliseconds.  The state U^n is not
+ * modified (stage 0 writes U1). */
+enoao_status enoao_time_sweep(enoao_ctx *ctx, int dir, int nrep, float *ms_per_launch);
+
 /* Times every supported tile shape of every axis on the current state
  * (restored afterwards) with CUDA events and keeps the fastest. */
 enoao_status enoao_autotune(enoao_ctx *ctx);

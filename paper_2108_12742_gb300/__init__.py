@@ -97,6 +97,8 @@ def load():
         "enoao_get_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
         "enoao_autotune": (ctypes.c_int, [P]),
+        "enoao_time_sweep": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -245,6 +247,12 @@ class Solver:
         a, b = ctypes.c_int(), ctypes.c_int()
         self._check(self._lib.enoao_get_tiles(self._h, d, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def time_sweep(self, d, nrep=10):
+        """Mean duration (ms) of one sweep-kernel launch along axis d (CUDA events)."""
+        ms = ctypes.c_float()
+        self._check(self._lib.enoao_time_sweep(self._h, d, nrep, ctypes.byref(ms)))
+        return ms.value
 
     def autotune(self):
         self._check(self._lib.enoao_autotune(self._h))

@@ -764,6 +764,31 @@ enoao_status enoao_get_tiles(const enoao_ctx* c, int dir, int* ta, int* ts) {
   return ENOAO_OK;
 }
 
+enoao_status enoao_time_sweep(enoao_ctx* c, int dir, int nrep, float* ms) {
+  if (!c || !ms) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch || dir < 0 || dir >= c->cfg.ndim) return fail(c, ENOAO_EINVAL, "dir out of range");
+  if (nrep < 1) return fail(c, ENOAO_EINVAL, "nrep must be >= 1");
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  alpha_current_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
+  // the last axis combines; earlier axes store L(u) exactly as inside a step
+  const int nd = c->cfg.ndim;
+  const int mode = dir < nd - 1 ? (kModeRhsStore | (dir > 0 ? kModeRhsAdd : 0))
+                                : (kModeCombine | (nd > 1 ? kModeRhsAdd : 0));
+  r = launch_sweep(c, dir, 0, mode, c->U[0], c->U[1], nullptr, nullptr);  // warm-up
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaEventRecord(c->t0, c->s));
+  for (int k = 0; k < nrep && r == ENOAO_OK; ++k)
+    r = launch_sweep(c, dir, 0, mode, c->U[0], c->U[1], nullptr, nullptr);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaEventRecord(c->t1, c->s));
+  CU(c, cudaEventSynchronize(c->t1));
+  float total = 0.f;
+  CU(c, cudaEventElapsedTime(&total, c->t0, c->t1));
+  *ms = total / nrep;
+  return leave(c);
+}
+
 enoao_status enoao_autotune(enoao_ctx* c) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
   if (c->batch) return ENOAO_OK;  // the batch kernel tunes itself at creation
