@@ -228,3 +228,71 @@ def test_errors_come_back_as_status_codes():
             s.rk_stage(3, 0.1)
         with pytest.raises(eno.EnoaoError):
             s.reconstruct_fluxes(1)
+
+
+# ---------------------------------------------------------------- FP32 bulk
+# The FP32-bulk path computes the reconstruction in FP32 from FP64 state
+# differences; its stated tolerances (relative to the field's max-norm) are
+# 1e-6 on interface fluxes and 1e-7 per step on the state, with at least
+# 99.9% of stencil choices equal to the FP64 oracle's.
+TOL32_FLUX = 1e-6
+TOL32_STEP = 1e-7
+
+
+@pytest.mark.parametrize("name", ["adv1d-square-ao7", "euler1d-riemann-ao5", "euler1d-riemann-ao7",
+                                  "euler2d-quad-ao5", "euler2d-random-ao7", "euler3d-blast-ao7"])
+def test_fp32_bulk_against_oracle(name):
+    s, P, U0 = _make(name, precision=eno.FP32_BULK)
+    with s:
+        s.init_state(U0)
+        agree = total = 0
+        for d in range(len(s.shape)):
+            F, idx = s.reconstruct_fluxes(d, want_idx=True)
+            Fo, io, _ = oracle.fluxes(P, U0, d, want_idx=True)
+            agree += int((idx == io).sum())
+            total += idx.size
+            assert relerr(F, Fo) <= TOL32_FLUX, (d, relerr(F, Fo))
+        assert agree / total >= 0.999, agree / total
+        s.advance(1e9, cfl=0.5, max_steps=1)
+        got = s.get_state()
+        ref = oracle.step(P, U0, s.stats().dt)
+        assert relerr(got, ref) <= TOL32_STEP, relerr(got, ref)
+
+
+# ------------------------------------------------- full size, bench launch config
+def test_full_size_2d_workload_sampled_patches():
+    # the 4096^2 benchmark workload, FP64, default tiles after autotune: one
+    # GPU step, then the oracle re-does that step on patches of the same input
+    # (with the full grid's alpha and dt); a patch keeps a 12-cell margin
+    # (three stages x the 4-cell reach of ENO-AO5) that is not compared.
+    import torch
+    n = 4096
+    U0 = inputs.euler2d_quadrants(n, n, seed=1)
+    with eno.Solver((n, n), (0.0, 0.0), (1.0, 1.0), system=eno.EULER, order=5,
+                    bc=eno.TRANSMISSIVE) as s:
+        dev = torch.from_numpy(U0).cuda()
+        s.init_state(dev)
+        s.autotune()
+        s.init_state(dev)
+        s.advance(1e9, cfl=0.5, max_steps=1)
+        st = s.stats()
+        out = torch.empty_like(dev)
+        s.get_state(out)
+        got = out.cpu().numpy()
+    rng = np.random.default_rng(0)
+    core, m = 32, 12
+    corners = [(0, 0), (n - core, n - core)] + [tuple(rng.integers(m, n - core - m, size=2))
+                                                for _ in range(3)]
+    # one patch across the quadrant split, where every stencil choice is exercised
+    xs = int(np.argmax(np.abs(np.diff(U0[0, 0, n // 2]))))
+    corners.append((max(m, xs - core // 2), n // 2))
+    for (x0, y0) in corners:
+        xa, xb = max(0, x0 - m), min(n, x0 + core + m)
+        ya, yb = max(0, y0 - m), min(n, y0 + core + m)
+        blk = np.ascontiguousarray(U0[:, :, ya:yb, xa:xb])
+        P = oracle.make_problem((xb - xa, yb - ya), (0.0, 0.0),
+                                ((xb - xa) / n, (yb - ya) / n), system=oracle.EULER, order=5)
+        ref = oracle.step_alpha(P, blk, st.dt, np.array(st.alpha[:]))
+        r = ref[:, :, y0 - ya:y0 - ya + core, x0 - xa:x0 - xa + core]
+        g = got[:, :, y0:y0 + core, x0:x0 + core]
+        assert relerr(g, r) <= TOL64, ((x0, y0), relerr(g, r))
