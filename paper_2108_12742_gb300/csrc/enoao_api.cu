@@ -272,6 +272,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
     a.dx_all[k] = c->dx[k];
   }
   a.ncell = c->ncell;
+  a.cstride = c->ncell;
   a.ndim = c->cfg.ndim;
   a.dir = d;
   a.bc = c->cfg.bc[d];

@@ -52,6 +52,7 @@ struct SweepArgs {
   StepState* st;
   long long n[3];       // cells per axis
   long long ncell;      // total cells
+  long long cstride;    // distance between two conserved components in the state arrays
   int ndim;
   int dir;              // swept axis
   int bc;               // boundary condition along dir

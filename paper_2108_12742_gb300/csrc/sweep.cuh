@@ -359,16 +359,22 @@ __device__ __forceinline__ TileGeo tile_geo(const SweepArgs& A, long long tile) 
   return g;
 }
 
-template <int NV>
+// Loads the permuted state of one cell.  COHERENT loads go through L2 (the
+// batched kernel reads states it wrote itself); otherwise the read-only
+// path is used (a sweep never writes the array it stencils from).
+template <int NV, bool COHERENT = false>
 __device__ __forceinline__ void load_state(const double* __restrict__ U, long long ncell,
                                            long long cell, int dir, double (&q)[NV]) {
 #pragma unroll
-  for (int c = 0; c < NV; ++c) q[c] = __ldg(U + perm_comp<NV>(c, dir) * ncell + cell);
+  for (int c = 0; c < NV; ++c) {
+    const double* p = U + perm_comp<NV>(c, dir) * ncell + cell;
+    q[c] = COHERENT ? __ldcg(p) : __ldg(p);
+  }
 }
 
 // FP64 re-decision of one FP32 choice: rebuilds the projected window of face
 // j+1/2 (global cell index sj of cell j along the line) from the FP64 state.
-template <int NV, int ORDER>
+template <int NV, int ORDER, bool COHERENT>
 __device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& g, int a,
                                              long long sj, int v, int sign, double alpha) {
   constexpr int G = Geo<ORDER>::G;
@@ -379,7 +385,7 @@ __device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& 
     const long long s = bc_map(sj - G + 1 + k, g.nd, A.bc);
     const long long cell = g.base + (g.a0 + a) * g.stride_a + s * g.stride_d;
     double t[NV];
-    load_state<NV>(A.u_in, A.ncell, cell, A.dir, t);
+    load_state<NV, COHERENT>(A.u_in, A.cstride, cell, A.dir, t);
 #pragma unroll
     for (int c = 0; c < NV; ++c) q[k][c] = t[c];
   }
@@ -435,16 +441,18 @@ struct NPrim {
   static constexpr int value = NV > 1 ? NV : 0;
 };
 
-template <int NV, int ORDER, typename R>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs A) {
+// One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
+// constant of the swept axis and the step size; amax accumulates |u_d| + c of
+// combined states (last stage), nfall counts FP64 re-decisions.
+template <int NV, int ORDER, typename R, bool COHERENT = false>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
+                                           unsigned char* smem_raw, double alpha_d, double dt,
+                                           double (&amax)[3], unsigned long long& nfall) {
   using GE = Geo<ORDER>;
   constexpr int G = GE::G;
   constexpr bool FP32 = sizeof(R) == 4;
   constexpr int NP = NPrim<NV>::value;
   StepState* st = A.st;
-  if (st->skip) return;
-
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TA = A.ta, TS = A.ts;
   const int SE = TS + 2 * G;
   const int cells = TA * SE;
@@ -456,277 +464,283 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs A) {
 
   const int dir = A.dir;
   const bool sfast = dir == 0;
-  const double alpha_d = st->alpha[dir];
   const R alpha = (R)alpha_d;
   const R gm1 = (R)(A.gamma - 1.0);
   const R adv = (R)A.adv_speed;
   const R delta = (R)A.delta;
   const R tie_rel = (R)A.tie_rel;
-  const double dt = st->dt;
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
+  auto sidx = [&](int a, int e) { return sfast ? a * SE + e : e * TA + a; };
+  (void)TS;
+  const int nts = g.nts;
+  const int sext = nts + 2 * G;  // extended cells in use
 
+  // ---------------- phase 1: split differences and Roe ingredients
+  {
+    const int cnt = sext;
+    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+      const int e = sfast ? it % cnt : it / TA;
+      const int a = sfast ? it / cnt : it % TA;
+      if (g.a0 + a >= g.na) continue;
+      const long long la = g.base + (g.a0 + a) * g.stride_a;
+      const long long sa = bc_map(g.s0 - G + e, g.nd, A.bc);
+      double qa64[NV];
+      load_state<NV, COHERENT>(A.u_in, A.cstride, la + sa * g.stride_d, dir, qa64);
+      R qa[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) qa[c] = (R)qa64[c];
+      const int si = sidx(a, e);
+      if constexpr (NP > 0) {
+        if (e >= G - 1 && e <= G + nts) {
+          R pr[NV];
+          roe_prims<NV, R>(qa, gm1, pr);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) prim[c * cells + si] = pr[c];
+        }
+      }
+      if (e + 1 < cnt) {
+        const long long sb = bc_map(g.s0 - G + e + 1, g.nd, A.bc);
+        double qb64[NV];
+        load_state<NV, COHERENT>(A.u_in, A.cstride, la + sb * g.stride_d, dir, qb64);
+        R qb[NV], dq[NV], dF[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          qb[c] = (R)qb64[c];
+          dq[c] = (R)(qb64[c] - qa64[c]);
+        }
+        flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
+        R m = R(0);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const R p = R(0.5) * (dF[c] + alpha * dq[c]);
+          const R n = R(0.5) * (dF[c] - alpha * dq[c]);
+          dfp[c * cells + si] = p;
+          dfm[c * cells + si] = n;
+          if constexpr (FP32) m = fmaxf(m, fmaxf(fabsf(p), fabsf(n)));
+        }
+        if constexpr (FP32) mx[si] = m;
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------- phase 2: per face choice and back-projection
+  {
+    const int cnt = nts + 1;
+    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+      const int f = sfast ? it % cnt : it / TA;
+      const int a = sfast ? it / cnt : it % TA;
+      if (g.a0 + a >= g.na) continue;
+      const int j = G - 1 + f;  // face j+1/2 in extended cells
+      Eigen<NV, R> E;
+      if constexpr (NV > 1) {
+        R pl[NV], prr[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          pl[c] = prim[c * cells + sidx(a, j)];
+          prr[c] = prim[c * cells + sidx(a, j + 1)];
+        }
+        roe_eigen<NV, R>(pl, prr, gm1, E);
+      }
+      R M = R(0);
+      if constexpr (FP32) {
+#pragma unroll
+        for (int e = j - G + 1; e <= j + G - 1; ++e) M = fmaxf(M, mx[sidx(a, e)]);
+      }
+      const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
+      const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
+      R C[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) C[c] = R(0);
+#pragma unroll 1
+      for (int v = 0; v < NV; ++v) {
+        R L[NV];
+        if constexpr (NV > 1) {
+          left_row<NV, R>(E, v, L);
+        } else {
+          L[0] = R(1);
+        }
+        R dp[8], dm[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dp[i] = dm[i] = R(0);
+#pragma unroll
+        for (int i = GE::LO; i <= GE::HI; ++i) {
+          const int ep = sidx(a, j - 4 + i);
+          const int em = sidx(a, j + 4 - i);
+          R sp = R(0), sm = R(0);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            sp += L[c] * dfp[c * cells + ep];
+            sm += L[c] * dfm[c * cells + em];
+          }
+          dp[i] = sp;
+          dm[i] = -sm;
+        }
+        R tol = R(0);
+        if constexpr (FP32) {
+          R ln = R(0);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
+          tol = R(1 << ORDER) * FLT_EPSILON * ln * M;
+        }
+        int ip, im;
+        bool mp = false, mm = false;
+        R cp = eno_select<ORDER, R, FP32>(dp, delta, tie_rel, tol, ip, mp);
+        R cm = eno_select<ORDER, R, FP32>(dm, delta, tie_rel, tol, im, mm);
+        if constexpr (FP32) {
+          if (mp || mm) {
+            const long long sj = g.s0 + f - 1;
+            if (mp) {
+              ip = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, sj, v, 0, alpha_d);
+              cp = R(0);
+#pragma unroll
+              for (int i = GE::LO; i <= GE::HI; ++i) cp += bcoef<R>(ip, i) * dp[i];
+              ++nfall;
+            }
+            if (mm) {
+              im = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, sj, v, 1, alpha_d);
+              cm = R(0);
+#pragma unroll
+              for (int i = GE::LO; i <= GE::HI; ++i) cm += bcoef<R>(im, i) * dm[i];
+              ++nfall;
+            }
+          }
+        }
+        if ((mode & kModeFlux) && A.idx_out && own) {
+          const long long nf = A.ncell / g.nd * (g.nd + 1);
+          const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+          A.idx_out[(v * 2 + 0) * nf + fc] = (int8_t)ip;
+          A.idx_out[(v * 2 + 1) * nf + fc] = (int8_t)im;
+        }
+        const R cv = cp + cm;
+        if constexpr (NV > 1) {
+          R Rc[NV];
+          right_col<NV, R>(E, v, Rc);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) C[c] += Rc[c] * cv;
+        } else {
+          C[0] += cv;
+        }
+      }
+      const int sj = sidx(a, j);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) Cf[c * cells + sj] = C[c];
+    }
+  }
+  __syncthreads();
+
+  // ---------------- phase 3: flux difference and Runge-Kutta combine
+  if (mode & kModeFlux) {
+    const int cnt = nts + 1;
+    const long long nf = A.ncell / g.nd * (g.nd + 1);
+    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+      const int f = sfast ? it % cnt : it / TA;
+      const int a = sfast ? it / cnt : it % TA;
+      if (g.a0 + a >= g.na) continue;
+      const long long gface = g.s0 + f;
+      if (!((gface <= g.nd) && (f < A.ts || gface == g.nd))) continue;
+      const int j = G - 1 + f;
+      const long long la = g.base + (g.a0 + a) * g.stride_a;
+      double ql[NV], qr[NV], Fl[NV], Fr[NV];
+      load_state<NV, COHERENT>(A.u_in, A.cstride, la + bc_map(gface - 1, g.nd, A.bc) * g.stride_d, dir, ql);
+      load_state<NV, COHERENT>(A.u_in, A.cstride, la + bc_map(gface, g.nd, A.bc) * g.stride_d, dir, qr);
+      phys_flux<NV>(ql, A.gamma - 1.0, A.adv_speed, Fl);
+      phys_flux<NV>(qr, A.gamma - 1.0, A.adv_speed, Fr);
+      const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
+        const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
+        A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + (double)Cf[c * cells + sidx(a, j)];
+      }
+    }
+  } else {
+    const int cnt = nts;
+    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+      const int t = sfast ? it % cnt : it / TA;
+      const int a = sfast ? it / cnt : it % TA;
+      if (g.a0 + a >= g.na) continue;
+      const int e = G + t;
+      const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
+      R r[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const R s = dfp[c * cells + sidx(a, e - 1)] + dfm[c * cells + sidx(a, e)] +
+                    (Cf[c * cells + sidx(a, e)] - Cf[c * cells + sidx(a, e - 1)]);
+        r[c] = -s * (R)inv_dx;
+      }
+      if (!(mode & kModeCombine)) {
+        R* rb = reinterpret_cast<R*>(A.rhs);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
+          rb[k] = (mode & kModeRhsAdd) ? rb[k] + r[c] : r[c];
+        }
+        continue;
+      }
+      double unew[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
+        double Lk;
+        if (mode & kModeRhsAdd) {
+          Lk = (double)(reinterpret_cast<const R*>(A.rhs)[k]) + (double)r[c];
+        } else {
+          Lk = (double)r[c];
+        }
+        const double ui = A.u_in[k];
+        double un;
+        if (A.stage == 0) {
+          un = ui + dt * Lk;
+        } else if (A.stage == 1) {
+          un = 0.75 * A.u0[k] + 0.25 * (ui + dt * Lk);
+        } else {
+          un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
+        }
+        A.u_out[k] = un;
+        unew[perm_comp<NV>(c, dir)] = un;  // back in conserved order
+      }
+      if constexpr (NV > 1) {
+        // non-physical check and next-step alpha on the new state
+        const double rho = unew[0];
+        double m2 = 0.0;
+#pragma unroll
+        for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
+        const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 / rho);
+        const bool ok = rho > 0.0 && p > 0.0 && isfinite(p);
+        if (!ok) {
+          atomicOr(&st->err, kErrNonPhys);
+          atomicMin(&st->err_cell, cell);
+        } else if ((mode & kModeAlpha) && A.stage == 2) {
+          const double cs = sqrt(A.gamma * p / rho);
+#pragma unroll
+          for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
+        }
+      } else {
+        if (!isfinite(unew[0])) {
+          atomicOr(&st->err, kErrNonPhys);
+          atomicMin(&st->err_cell, cell);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int NV, int ORDER, typename R>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs A) {
+  constexpr bool FP32 = sizeof(R) == 4;
+  StepState* st = A.st;
+  if (st->skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int mode = A.mode;
+  const double alpha_d = st->alpha[A.dir];
+  const double dt = st->dt;
   double amax[3] = {0.0, 0.0, 0.0};
   unsigned long long nfall = 0;
-
-  auto sidx = [&](int a, int e) { return sfast ? a * SE + e : e * TA + a; };
-
-  for (long long tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
-    const TileGeo g = tile_geo(A, tile);
-    const int nts = g.nts;
-    const int sext = nts + 2 * G;  // extended cells in use
-
-    // ---------------- phase 1: split differences and Roe ingredients
-    {
-      const int cnt = sext;
-      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-        const int e = sfast ? it % cnt : it / TA;
-        const int a = sfast ? it / cnt : it % TA;
-        if (g.a0 + a >= g.na) continue;
-        const long long la = g.base + (g.a0 + a) * g.stride_a;
-        const long long sa = bc_map(g.s0 - G + e, g.nd, A.bc);
-        double qa64[NV];
-        load_state<NV>(A.u_in, A.ncell, la + sa * g.stride_d, dir, qa64);
-        R qa[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) qa[c] = (R)qa64[c];
-        const int si = sidx(a, e);
-        if constexpr (NP > 0) {
-          if (e >= G - 1 && e <= G + nts) {
-            R pr[NV];
-            roe_prims<NV, R>(qa, gm1, pr);
-#pragma unroll
-            for (int c = 0; c < NV; ++c) prim[c * cells + si] = pr[c];
-          }
-        }
-        if (e + 1 < cnt) {
-          const long long sb = bc_map(g.s0 - G + e + 1, g.nd, A.bc);
-          double qb64[NV];
-          load_state<NV>(A.u_in, A.ncell, la + sb * g.stride_d, dir, qb64);
-          R qb[NV], dq[NV], dF[NV];
-#pragma unroll
-          for (int c = 0; c < NV; ++c) {
-            qb[c] = (R)qb64[c];
-            dq[c] = (R)(qb64[c] - qa64[c]);
-          }
-          flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
-          R m = R(0);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) {
-            const R p = R(0.5) * (dF[c] + alpha * dq[c]);
-            const R n = R(0.5) * (dF[c] - alpha * dq[c]);
-            dfp[c * cells + si] = p;
-            dfm[c * cells + si] = n;
-            if constexpr (FP32) m = fmaxf(m, fmaxf(fabsf(p), fabsf(n)));
-          }
-          if constexpr (FP32) mx[si] = m;
-        }
-      }
-    }
-    __syncthreads();
-
-    // ---------------- phase 2: per face choice and back-projection
-    {
-      const int cnt = nts + 1;
-      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-        const int f = sfast ? it % cnt : it / TA;
-        const int a = sfast ? it / cnt : it % TA;
-        if (g.a0 + a >= g.na) continue;
-        const int j = G - 1 + f;  // face j+1/2 in extended cells
-        Eigen<NV, R> E;
-        if constexpr (NV > 1) {
-          R pl[NV], prr[NV];
-#pragma unroll
-          for (int c = 0; c < NV; ++c) {
-            pl[c] = prim[c * cells + sidx(a, j)];
-            prr[c] = prim[c * cells + sidx(a, j + 1)];
-          }
-          roe_eigen<NV, R>(pl, prr, gm1, E);
-        }
-        R M = R(0);
-        if constexpr (FP32) {
-#pragma unroll
-          for (int e = j - G + 1; e <= j + G - 1; ++e) M = fmaxf(M, mx[sidx(a, e)]);
-        }
-        const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
-        const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
-        R C[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) C[c] = R(0);
-#pragma unroll 1
-        for (int v = 0; v < NV; ++v) {
-          R L[NV];
-          if constexpr (NV > 1) {
-            left_row<NV, R>(E, v, L);
-          } else {
-            L[0] = R(1);
-          }
-          R dp[8], dm[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) dp[i] = dm[i] = R(0);
-#pragma unroll
-          for (int i = GE::LO; i <= GE::HI; ++i) {
-            const int ep = sidx(a, j - 4 + i);
-            const int em = sidx(a, j + 4 - i);
-            R sp = R(0), sm = R(0);
-#pragma unroll
-            for (int c = 0; c < NV; ++c) {
-              sp += L[c] * dfp[c * cells + ep];
-              sm += L[c] * dfm[c * cells + em];
-            }
-            dp[i] = sp;
-            dm[i] = -sm;
-          }
-          R tol = R(0);
-          if constexpr (FP32) {
-            R ln = R(0);
-#pragma unroll
-            for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
-            tol = R(1 << ORDER) * FLT_EPSILON * ln * M;
-          }
-          int ip, im;
-          bool mp = false, mm = false;
-          R cp = eno_select<ORDER, R, FP32>(dp, delta, tie_rel, tol, ip, mp);
-          R cm = eno_select<ORDER, R, FP32>(dm, delta, tie_rel, tol, im, mm);
-          if constexpr (FP32) {
-            if (mp || mm) {
-              const long long sj = g.s0 + f - 1;
-              if (mp) {
-                ip = redo_choice_fp64<NV, ORDER>(A, g, a, sj, v, 0, alpha_d);
-                cp = R(0);
-#pragma unroll
-                for (int i = GE::LO; i <= GE::HI; ++i) cp += bcoef<R>(ip, i) * dp[i];
-                ++nfall;
-              }
-              if (mm) {
-                im = redo_choice_fp64<NV, ORDER>(A, g, a, sj, v, 1, alpha_d);
-                cm = R(0);
-#pragma unroll
-                for (int i = GE::LO; i <= GE::HI; ++i) cm += bcoef<R>(im, i) * dm[i];
-                ++nfall;
-              }
-            }
-          }
-          if ((mode & kModeFlux) && A.idx_out && own) {
-            const long long nf = A.ncell / g.nd * (g.nd + 1);
-            const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
-            A.idx_out[(v * 2 + 0) * nf + fc] = (int8_t)ip;
-            A.idx_out[(v * 2 + 1) * nf + fc] = (int8_t)im;
-          }
-          const R cv = cp + cm;
-          if constexpr (NV > 1) {
-            R Rc[NV];
-            right_col<NV, R>(E, v, Rc);
-#pragma unroll
-            for (int c = 0; c < NV; ++c) C[c] += Rc[c] * cv;
-          } else {
-            C[0] += cv;
-          }
-        }
-        const int sj = sidx(a, j);
-#pragma unroll
-        for (int c = 0; c < NV; ++c) Cf[c * cells + sj] = C[c];
-      }
-    }
-    __syncthreads();
-
-    // ---------------- phase 3: flux difference and Runge-Kutta combine
-    if (mode & kModeFlux) {
-      const int cnt = nts + 1;
-      const long long nf = A.ncell / g.nd * (g.nd + 1);
-      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-        const int f = sfast ? it % cnt : it / TA;
-        const int a = sfast ? it / cnt : it % TA;
-        if (g.a0 + a >= g.na) continue;
-        const long long gface = g.s0 + f;
-        if (!((gface <= g.nd) && (f < A.ts || gface == g.nd))) continue;
-        const int j = G - 1 + f;
-        const long long la = g.base + (g.a0 + a) * g.stride_a;
-        double ql[NV], qr[NV], Fl[NV], Fr[NV];
-        load_state<NV>(A.u_in, A.ncell, la + bc_map(gface - 1, g.nd, A.bc) * g.stride_d, dir, ql);
-        load_state<NV>(A.u_in, A.ncell, la + bc_map(gface, g.nd, A.bc) * g.stride_d, dir, qr);
-        phys_flux<NV>(ql, A.gamma - 1.0, A.adv_speed, Fl);
-        phys_flux<NV>(qr, A.gamma - 1.0, A.adv_speed, Fr);
-        const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
-          const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
-          A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + (double)Cf[c * cells + sidx(a, j)];
-        }
-      }
-    } else {
-      const int cnt = nts;
-      for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-        const int t = sfast ? it % cnt : it / TA;
-        const int a = sfast ? it / cnt : it % TA;
-        if (g.a0 + a >= g.na) continue;
-        const int e = G + t;
-        const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
-        R r[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          const R s = dfp[c * cells + sidx(a, e - 1)] + dfm[c * cells + sidx(a, e)] +
-                      (Cf[c * cells + sidx(a, e)] - Cf[c * cells + sidx(a, e - 1)]);
-          r[c] = -s * (R)inv_dx;
-        }
-        if (!(mode & kModeCombine)) {
-          R* rb = reinterpret_cast<R*>(A.rhs);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) {
-            const long long k = perm_comp<NV>(c, dir) * A.ncell + cell;
-            rb[k] = (mode & kModeRhsAdd) ? rb[k] + r[c] : r[c];
-          }
-          continue;
-        }
-        double unew[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          const long long k = perm_comp<NV>(c, dir) * A.ncell + cell;
-          double Lk;
-          if (mode & kModeRhsAdd) {
-            Lk = (double)(reinterpret_cast<const R*>(A.rhs)[k]) + (double)r[c];
-          } else {
-            Lk = (double)r[c];
-          }
-          const double ui = A.u_in[k];
-          double un;
-          if (A.stage == 0) {
-            un = ui + dt * Lk;
-          } else if (A.stage == 1) {
-            un = 0.75 * A.u0[k] + 0.25 * (ui + dt * Lk);
-          } else {
-            un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
-          }
-          A.u_out[k] = un;
-          unew[perm_comp<NV>(c, dir)] = un;  // back in conserved order
-        }
-        if constexpr (NV > 1) {
-          // non-physical check and next-step alpha on the new state
-          const double rho = unew[0];
-          double m2 = 0.0;
-#pragma unroll
-          for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
-          const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 / rho);
-          const bool ok = rho > 0.0 && p > 0.0 && isfinite(p);
-          if (!ok) {
-            atomicOr(&st->err, kErrNonPhys);
-            atomicMin(&st->err_cell, cell);
-          } else if ((mode & kModeAlpha) && A.stage == 2) {
-            const double cs = sqrt(A.gamma * p / rho);
-#pragma unroll
-            for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
-          }
-        } else {
-          if (!isfinite(unew[0])) {
-            atomicOr(&st->err, kErrNonPhys);
-            atomicMin(&st->err_cell, cell);
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
+  for (long long tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x)
+    sweep_tile<NV, ORDER, R>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax, nfall);
 
   if constexpr (FP32) {
     if (nfall) atomicAdd(&st->fallbacks, nfall);
