@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "enoao.h"
+#include "enoao_ctx.h"
 #include "enoao_internal.h"
 #include "sweep.cuh"
 
@@ -154,6 +155,9 @@ struct BatchState {
   int ts = 256, block = 256;
   long long steps = 0;
   std::vector<long long> off_h;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_steps = 0;
+  double graph_cfl = 0.0;
 };
 
 namespace {
@@ -192,10 +196,300 @@ cudaError_t launch_batch(int nv, int order, int fp32, const BatchArgs& b, int bl
 
 }  // namespace
 
-// ---- entry points used by enoao_api.cu (the context owns the stream,
-// the step state and the error string).
-struct BatchHooks {
-  static enoao_ctx* ctx;
-};
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+enoao_status bfail(enoao_ctx* c, enoao_status st, const std::string& msg) {
+  c->err = msg;
+  return st;
+}
+
+#define BCU(c, call)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return bfail((c), ENOAO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+__global__ void batch_reset_kernel(StepState* st) {
+  st->err = 0;
+  st->err_cell = 0x7fffffffffffffffll;
+  st->fallbacks = 0;
+  st->skip = 0;
+}
+
+// rho > 0 and p > 0 of every cell of the concatenated 1D Euler states.
+__global__ void batch_check_kernel(const double* U, long long total, double gamma, StepState* st) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double rho = U[i], m = U[total + i], E = U[2 * total + i];
+    const double p = (gamma - 1.0) * (E - 0.5 * m * m / rho);
+    if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p)) {
+      atomicOr(&st->err, kErrNonPhys);
+      atomicMin(&st->err_cell, i);
+    }
+  }
+}
+
+BatchArgs make_args(enoao_ctx* c, int nsteps, double cfl) {
+  BatchState* b = c->batch;
+  BatchArgs a;
+  memset(&a, 0, sizeof a);
+  for (int k = 0; k < 3; ++k) a.U[k] = b->U[k];
+  a.total = b->total;
+  a.nprob = b->nprob;
+  a.nsteps = nsteps;
+  a.cfl = cfl;
+  a.order = b->order;
+  a.off = b->off;
+  a.n = b->n;
+  a.dx = b->dx;
+  a.t = b->t;
+  a.alpha = b->alpha;
+  a.dt = b->dt;
+  a.queue = b->queue;
+  a.st = c->st;
+  a.ts = b->ts;
+  a.bc = c->cfg.bc[0];
+  a.gamma = c->cfg.gamma;
+  a.adv_speed = c->cfg.adv_speed;
+  a.delta = c->cfg.delta;
+  a.tie_rel = c->cfg.tie_rel;
+  return a;
+}
+
+enoao_status enqueue_batch(enoao_ctx* c, int nsteps, double cfl) {
+  BatchState* b = c->batch;
+  const int f32 = c->cfg.precision == ENOAO_FP32_BULK;
+  const size_t smem = sweep_smem_bytes(b->nv, c->cfg.order, f32, 1, b->ts);
+  cudaError_t e = launch_batch(b->nv, c->cfg.order, f32, make_args(c, nsteps, cfl), b->block, smem,
+                               c->sms, c->s);
+  if (e != cudaSuccess)
+    return bfail(c, ENOAO_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  return ENOAO_OK;
+}
+
+enoao_status stream_enter(enoao_ctx* c) {
+  BCU(c, cudaSetDevice(c->device));
+  BCU(c, cudaEventRecord(c->ev_a, c->user));
+  BCU(c, cudaStreamWaitEvent(c->s, c->ev_a, 0));
+  return ENOAO_OK;
+}
+
+enoao_status stream_leave(enoao_ctx* c) {
+  BCU(c, cudaEventRecord(c->ev_b, c->s));
+  BCU(c, cudaStreamWaitEvent(c->user, c->ev_b, 0));
+  return ENOAO_OK;
+}
+
+enoao_status read_err(enoao_ctx* c) {
+  BCU(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(StepState), cudaMemcpyDeviceToHost, c->s));
+  BCU(c, cudaStreamSynchronize(c->s));
+  if (c->st_host->err & kErrNonPhys)
+    return bfail(c, ENOAO_ENONPHYS,
+                 "non-physical state (rho <= 0, p <= 0 or NaN) at cell " +
+                     std::to_string((long long)c->st_host->err_cell));
+  return ENOAO_OK;
+}
+
+}  // namespace
+
+void batch_destroy(BatchState* b) {
+  if (!b) return;
+  for (int k = 0; k < 3; ++k) cudaFree(b->U[k]);
+  cudaFree(b->order);
+  cudaFree(b->off);
+  cudaFree(b->n);
+  cudaFree(b->dx);
+  cudaFree(b->t);
+  cudaFree(b->alpha);
+  cudaFree(b->dt);
+  cudaFree(b->queue);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  delete b;
+}
+
+enoao_status batch_create(enoao_ctx* c, const enoao_config* proto, int nprob, const int64_t* n,
+                          const double* lo, const double* hi) {
+  const int G = proto->order / 2 + 2;
+  std::vector<long long> off(nprob);
+  std::vector<int> nn(nprob), order(nprob);
+  std::vector<double> dx(nprob);
+  long long total = 0;
+  for (int i = 0; i < nprob; ++i) {
+    if (n[i] < 2 * G + 1 || n[i] > (1 << 30))
+      return bfail(c, ENOAO_EINVAL, "problem " + std::to_string(i) + " has " +
+                                        std::to_string((long long)n[i]) + " cells; at least " +
+                                        std::to_string(2 * G + 1) + " are needed");
+    if (!(hi[i] > lo[i])) return bfail(c, ENOAO_EINVAL, "problem " + std::to_string(i) + ": hi <= lo");
+    off[i] = total;
+    nn[i] = (int)n[i];
+    dx[i] = (hi[i] - lo[i]) / (double)n[i];
+    total += n[i];
+  }
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nn[a] > nn[b]; });
+  BatchState* b = new BatchState;
+  c->batch = b;
+  b->nprob = nprob;
+  b->total = total;
+  b->nv = proto->system == ENOAO_EULER ? 3 : 1;
+  b->off_h = off;
+  b->ts = 256;
+  b->block = 256;
+  c->ncell = total;
+  const size_t sb = (size_t)b->nv * total * sizeof(double);
+  for (int k = 0; k < 3; ++k) BCU(c, cudaMalloc(&b->U[k], sb));
+  BCU(c, cudaMalloc(&b->order, nprob * sizeof(int)));
+  BCU(c, cudaMalloc(&b->off, nprob * sizeof(long long)));
+  BCU(c, cudaMalloc(&b->n, nprob * sizeof(int)));
+  BCU(c, cudaMalloc(&b->dx, nprob * sizeof(double)));
+  BCU(c, cudaMalloc(&b->t, nprob * sizeof(double)));
+  BCU(c, cudaMalloc(&b->alpha, nprob * sizeof(double)));
+  BCU(c, cudaMalloc(&b->dt, nprob * sizeof(double)));
+  BCU(c, cudaMalloc(&b->queue, sizeof(int)));
+  BCU(c, cudaMemcpy(b->order, order.data(), nprob * sizeof(int), cudaMemcpyHostToDevice));
+  BCU(c, cudaMemcpy(b->off, off.data(), nprob * sizeof(long long), cudaMemcpyHostToDevice));
+  BCU(c, cudaMemcpy(b->n, nn.data(), nprob * sizeof(int), cudaMemcpyHostToDevice));
+  BCU(c, cudaMemcpy(b->dx, dx.data(), nprob * sizeof(double), cudaMemcpyHostToDevice));
+  BCU(c, cudaMemset(b->t, 0, nprob * sizeof(double)));
+  BCU(c, cudaMemset(b->alpha, 0, nprob * sizeof(double)));
+  BCU(c, cudaMemset(b->dt, 0, nprob * sizeof(double)));
+  return ENOAO_OK;
+}
+
+enoao_status batch_init_state(enoao_ctx* c, const double* U, int on_device) {
+  BatchState* b = c->batch;
+  enoao_status r = stream_enter(c);
+  if (r != ENOAO_OK) return r;
+  BCU(c, cudaMemcpyAsync(b->U[0], U, (size_t)b->nv * b->total * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+  BCU(c, cudaMemsetAsync(b->t, 0, b->nprob * sizeof(double), c->s));
+  batch_reset_kernel<<<1, 1, 0, c->s>>>(c->st);
+  if (b->nv == 3)
+    batch_check_kernel<<<std::max(1, std::min<int>((int)((b->total + 255) / 256), c->sms * 8)), 256,
+                         0, c->s>>>(b->U[0], b->total, c->cfg.gamma, c->st);
+  BCU(c, cudaGetLastError());
+  b->steps = 0;
+  r = stream_leave(c);
+  if (r != ENOAO_OK) return r;
+  return read_err(c);
+}
+
+enoao_status batch_get_state(enoao_ctx* c, double* U, int on_device) {
+  BatchState* b = c->batch;
+  enoao_status r = stream_enter(c);
+  if (r != ENOAO_OK) return r;
+  BCU(c, cudaMemcpyAsync(U, b->U[0], (size_t)b->nv * b->total * sizeof(double),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  r = stream_leave(c);
+  if (r != ENOAO_OK) return r;
+  BCU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+// One CUDA graph holds the queue reset and the persistent launch for a given
+// (nsteps, cfl); replays reuse it.
+enoao_status batch_advance(enoao_ctx* c, int64_t nsteps, double cfl, bool sync) {
+  BatchState* b = c->batch;
+  if (nsteps > (1 << 30)) return bfail(c, ENOAO_EINVAL, "nsteps too large");
+  enoao_status r = stream_enter(c);
+  if (r != ENOAO_OK) return r;
+  if (!b->graph || b->graph_steps != nsteps || b->graph_cfl != cfl) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaGraph_t g;
+    BCU(c, cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+    r = enqueue_batch(c, (int)nsteps, cfl);
+    cudaError_t e = cudaStreamEndCapture(c->s, &g);
+    if (r != ENOAO_OK) return r;
+    if (e != cudaSuccess) return bfail(c, ENOAO_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(c, ENOAO_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    b->graph_steps = nsteps;
+    b->graph_cfl = cfl;
+  }
+  BCU(c, cudaGraphLaunch(b->graph, c->s));
+  b->steps += nsteps;
+  r = stream_leave(c);
+  if (r != ENOAO_OK) return r;
+  if (!sync) return ENOAO_OK;
+  return read_err(c);
+}
+
+enoao_status batch_stats(enoao_ctx* c, enoao_stats* out) {
+  BatchState* b = c->batch;
+  enoao_status r = read_err(c);
+  if (r != ENOAO_OK && r != ENOAO_ENONPHYS) return r;
+  double t0 = 0.0, a0 = 0.0, d0 = 0.0;
+  BCU(c, cudaMemcpy(&t0, b->t, sizeof(double), cudaMemcpyDeviceToHost));
+  BCU(c, cudaMemcpy(&a0, b->alpha, sizeof(double), cudaMemcpyDeviceToHost));
+  BCU(c, cudaMemcpy(&d0, b->dt, sizeof(double), cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof *out);
+  out->t = t0;
+  out->steps = b->steps;
+  out->alpha[0] = a0;
+  out->dt = d0;
+  out->fp64_fallbacks = c->st_host->fallbacks;
+  return ENOAO_OK;
+}
+
+// Times one step of the whole batch for each (tile, block) candidate on a
+// saved copy of the state and keeps the fastest.
+enoao_status batch_autotune(enoao_ctx* c) {
+  BatchState* b = c->batch;
+  const size_t sb = (size_t)b->nv * b->total * sizeof(double);
+  double* save = nullptr;
+  double* tsave = nullptr;
+  BCU(c, cudaMalloc(&save, sb));
+  cudaError_t e0 = cudaMalloc(&tsave, b->nprob * sizeof(double));
+  if (e0 != cudaSuccess) {
+    cudaFree(save);
+    return bfail(c, ENOAO_ENOMEM, "autotune scratch");
+  }
+  enoao_status r = stream_enter(c);
+  const int cands[][2] = {{128, 128}, {256, 128}, {256, 256}, {512, 256}};
+  float best = 1e30f;
+  int bts = b->ts, bblk = b->block;
+  if (r == ENOAO_OK) {
+    cudaMemcpyAsync(save, b->U[0], sb, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(tsave, b->t, b->nprob * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
+    for (auto& cd : cands) {
+      b->ts = cd[0];
+      b->block = cd[1];
+      cudaEventRecord(c->t0, c->s);
+      enoao_status rr = enqueue_batch(c, 1, 0.5);
+      cudaEventRecord(c->t1, c->s);
+      cudaMemcpyAsync(b->U[0], save, sb, cudaMemcpyDeviceToDevice, c->s);
+      if (rr != ENOAO_OK || cudaEventSynchronize(c->t1) != cudaSuccess) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->t0, c->t1);
+      if (ms < best) {
+        best = ms;
+        bts = cd[0];
+        bblk = cd[1];
+      }
+    }
+    cudaMemcpyAsync(b->t, tsave, b->nprob * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
+    cudaStreamSynchronize(c->s);
+    c->err.clear();
+  }
+  b->ts = bts;
+  b->block = bblk;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaFree(save);
+  cudaFree(tsave);
+  if (r != ENOAO_OK) return r;
+  r = stream_leave(c);
+  if (r != ENOAO_OK) return r;
+  return read_err(c);
+}
 
 }  // namespace enoao

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "enoao.h"
+#include "enoao_ctx.h"
 #include "enoao_internal.h"
 
 using namespace enoao;
@@ -23,37 +24,6 @@ thread_local std::string g_create_error;
 
 // Batched-problem state (defined with the batch kernels).
 }  // namespace
-
-namespace enoao {
-struct BatchState;
-void batch_destroy(BatchState* b);
-enoao_status batch_create(enoao_ctx* ctx, const enoao_config* proto, int nprob,
-                          const int64_t* n, const double* lo, const double* hi);
-enoao_status batch_advance(enoao_ctx* ctx, int64_t nsteps, double cfl, bool sync);
-enoao_status batch_init_state(enoao_ctx* ctx, const double* U, int on_device);
-enoao_status batch_get_state(enoao_ctx* ctx, double* U, int on_device);
-}  // namespace enoao
-
-struct enoao_ctx {
-  enoao_config cfg{};
-  int nv = 0;
-  long long ncell = 0;
-  double dx[3] = {1, 1, 1};
-  cudaStream_t user = nullptr;   // caller's stream
-  cudaStream_t s = nullptr;      // library stream (non-blocking, capturable)
-  cudaEvent_t ev_a = nullptr, ev_b = nullptr, t0 = nullptr, t1 = nullptr;
-  double* U[3] = {nullptr, nullptr, nullptr};  // U^n, U1, U2
-  void* rhs = nullptr;
-  StepState* st = nullptr;       // device
-  StepState* st_host = nullptr;  // pinned mirror
-  int ta[3] = {0, 0, 0}, ts[3] = {0, 0, 0}, block[3] = {128, 128, 128};
-  int sms = 0;
-  cudaGraphExec_t graph = nullptr;
-  int graph_steps = 0;
-  std::string err;
-  BatchState* batch = nullptr;
-  int device = 0;
-};
 
 namespace {
 
@@ -724,6 +694,7 @@ enoao_status enoao_sync(enoao_ctx* c) {
 
 enoao_status enoao_get_stats(enoao_ctx* c, enoao_stats* out) {
   if (!c || !out) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return batch_stats(c, out);
   enoao_status r = read_host_state(c);
   if (r != ENOAO_OK) return r;
   const StepState& h = *c->st_host;
@@ -792,7 +763,7 @@ enoao_status enoao_time_sweep(enoao_ctx* c, int dir, int nrep, float* ms) {
 
 enoao_status enoao_autotune(enoao_ctx* c) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
-  if (c->batch) return ENOAO_OK;  // the batch kernel tunes itself at creation
+  if (c->batch) return batch_autotune(c);
   // Save the state; time one stage-0 sweep per candidate on the live state.
   const size_t bytes = (size_t)c->nv * c->ncell * sizeof(double);
   enoao_status r = enter(c);

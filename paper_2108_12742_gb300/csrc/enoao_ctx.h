@@ -1,0 +1,42 @@
+// Context of the C interface (host side), shared by the runtime units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "enoao.h"
+#include "enoao_internal.h"
+
+namespace enoao {
+struct BatchState;
+void batch_destroy(BatchState* b);
+enoao_status batch_create(enoao_ctx* ctx, const enoao_config* proto, int nprob,
+                          const int64_t* n, const double* lo, const double* hi);
+enoao_status batch_advance(enoao_ctx* ctx, int64_t nsteps, double cfl, bool sync);
+enoao_status batch_init_state(enoao_ctx* ctx, const double* U, int on_device);
+enoao_status batch_get_state(enoao_ctx* ctx, double* U, int on_device);
+enoao_status batch_stats(enoao_ctx* ctx, enoao_stats* out);
+enoao_status batch_autotune(enoao_ctx* ctx);
+}  // namespace enoao
+
+struct enoao_ctx {
+  enoao_config cfg{};
+  int nv = 0;
+  long long ncell = 0;
+  double dx[3] = {1, 1, 1};
+  cudaStream_t user = nullptr;   // caller's stream
+  cudaStream_t s = nullptr;      // library stream (non-blocking, capturable)
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, t0 = nullptr, t1 = nullptr;
+  double* U[3] = {nullptr, nullptr, nullptr};  // U^n, U1, U2
+  void* rhs = nullptr;
+  enoao::StepState* st = nullptr;       // device
+  enoao::StepState* st_host = nullptr;  // pinned mirror
+  int ta[3] = {0, 0, 0}, ts[3] = {0, 0, 0}, block[3] = {128, 128, 128};
+  int sms = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  std::string err;
+  enoao::BatchState* batch = nullptr;
+  int device = 0;
+};

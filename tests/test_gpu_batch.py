@@ -1,0 +1,98 @@
+"""Batched uneven 1D problems (one persistent launch) against the single-problem
+path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2108_12742_gb300 as eno
+from paper_2108_12742_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_12742_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _batch(sizes, seed, system=eno.EULER):
+    if system == eno.EULER:
+        return inputs.batch_states(sizes, seed)
+    return np.concatenate([inputs.advection_random(int(n), seed + i).reshape(1, -1)
+                           for i, n in enumerate(sizes)], axis=1)
+
+
+@pytest.mark.parametrize("precision", [eno.FP64, eno.FP32_BULK])
+@pytest.mark.parametrize("order", [5, 7])
+def test_batch_equals_single_problem_runs(precision, order):
+    sizes = np.array([11, 700, 257, 4099, 64, 1000, 33])
+    U = _batch(sizes, seed=100)
+    nsteps = 7
+    with eno.Batch(sizes, 0.0, 1.0, system=eno.EULER, order=order, precision=precision) as b:
+        b.init_state(U)
+        b.advance_steps(nsteps, 0.5)
+        got = b.get_state()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i, n in enumerate(sizes):
+        with eno.Solver((int(n),), (0.0,), (1.0,), system=eno.EULER, order=order,
+                        precision=precision) as s:
+            s.init_state(U[:, off[i]:off[i + 1]].reshape(3, 1, 1, -1))
+            s.advance_steps(nsteps, 0.5)
+            ref = s.get_state().reshape(3, -1)
+        assert np.array_equal(got[:, off[i]:off[i + 1]], ref), (i, int(n))
+
+
+def test_batch_step_matches_oracle():
+    sizes = np.array([300, 97, 1200])
+    U = _batch(sizes, seed=7)
+    with eno.Batch(sizes, 0.0, 1.0, system=eno.EULER, order=5) as b:
+        b.init_state(U)
+        b.advance_steps(1, 0.5)
+        got = b.get_state()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i, n in enumerate(sizes):
+        Ui = U[:, off[i]:off[i + 1]].reshape(3, 1, 1, -1)
+        P = oracle.make_problem((int(n),), (0.0,), (1.0,), system=oracle.EULER, order=5)
+        a = oracle.alpha(P, Ui)
+        dt = 0.5 / (a[0] / (1.0 / n))
+        ref = oracle.step(P, Ui, dt).reshape(3, -1)
+        g = got[:, off[i]:off[i + 1]]
+        assert np.abs(g - ref).max() / np.abs(ref).max() <= 1e-12, i
+
+
+def test_batch_scalar_periodic_and_autotune():
+    sizes = np.array([40, 129, 513])
+    U = _batch(sizes, seed=3, system=eno.SCALAR_ADVECTION)
+    with eno.Batch(sizes, -1.0, 1.0, system=eno.SCALAR_ADVECTION, order=7, bc=eno.PERIODIC) as b:
+        b.init_state(U)
+        b.autotune()
+        b.init_state(U)
+        b.advance_steps(5, 0.5)
+        got = b.get_state()
+        st = b.stats()
+    assert st.steps == 5
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i, n in enumerate(sizes):
+        P = oracle.make_problem((int(n),), (-1.0,), (1.0,), system=oracle.SCALAR, order=7,
+                                bc=oracle.PERIODIC)
+        ref, _, _ = oracle.advance(P, U[:, off[i]:off[i + 1]].reshape(1, 1, 1, -1), 1e9,
+                                   cfl=0.5, max_steps=5)
+        g = got[:, off[i]:off[i + 1]]
+        assert np.abs(g - ref.reshape(1, -1)).max() / np.abs(ref).max() <= 1e-12
+
+
+def test_batch_rejects_bad_input():
+    with pytest.raises(eno.EnoaoError):
+        eno.Batch(np.array([100, 5]), 0.0, 1.0)
+    sizes = np.array([50, 60])
+    U = _batch(sizes, seed=1)
+    U[0, 70] = -0.5
+    with eno.Batch(sizes, 0.0, 1.0) as b:
+        with pytest.raises(eno.EnoaoError) as e:
+            b.init_state(U)
+        assert e.value.status == 4 and "cell 70" in str(e.value)
