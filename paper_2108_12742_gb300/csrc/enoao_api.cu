@@ -200,18 +200,19 @@ bool fp32(const enoao_ctx* c) { return c->cfg.precision == ENOAO_FP32_BULK; }
 
 int halo(int order) { return order / 2 + 2; }
 
+// Tile lengths are 2^k - 1 cells so that the 2^k faces of a line fill whole
+// warps in the per-face phase.
 void default_tiles(enoao_ctx* c) {
   const bool f32 = fp32(c);
   for (int d = 0; d < c->cfg.ndim; ++d) {
     if (d == 0) {
       c->ta[d] = c->cfg.ndim == 1 ? 1 : 2;
-      c->ts[d] = f32 ? 128 : 64;
-      c->block[d] = 128;
+      c->ts[d] = f32 ? 127 : 63;
     } else {
       c->ta[d] = 32;
-      c->ts[d] = f32 ? 32 : 16;
-      c->block[d] = 128;
+      c->ts[d] = f32 ? 31 : 15;
     }
+    c->block[d] = 128;
   }
 }
 
@@ -774,13 +775,13 @@ enoao_status enoao_autotune(enoao_ctx* c) {
     std::vector<std::pair<int, int>> cands;
     if (d == 0) {
       const int tas[] = {1, 2, 4};
-      const int tss[] = {64, 128, 256};
+      const int tss[] = {63, 127, 255};
       for (int ta : tas)
         for (int ts : tss)
           if (c->cfg.ndim > 1 || ta == 1) cands.push_back({ta, ts});
     } else {
       const int tas[] = {16, 32, 64};
-      const int tss[] = {8, 16, 32, 64};
+      const int tss[] = {7, 15, 31, 63};
       for (int ta : tas)
         for (int ts : tss) cands.push_back({ta, ts});
     }

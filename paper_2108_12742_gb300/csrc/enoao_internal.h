@@ -30,6 +30,9 @@ struct StepState {
   long long err_cell;       // first cell (min index) that raised kErrNonPhys
   unsigned long long fallbacks;  // FP32-bulk decisions re-done in FP64
   unsigned long long decisions;  // stencil decisions taken
+  unsigned long long tile_next;  // dynamic tile queue of the running sweep launch
+  unsigned int blocks_done;      // blocks of the running sweep launch that have left it
+  unsigned int pad2;
 };
 
 constexpr int kErrNonPhys = 1;

@@ -561,22 +561,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         } else {
           L[0] = R(1);
         }
-        R dp[8], dm[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) dp[i] = dm[i] = R(0);
-#pragma unroll
-        for (int i = GE::LO; i <= GE::HI; ++i) {
-          const int ep = sidx(a, j - 4 + i);
-          const int em = sidx(a, j + 4 - i);
-          R sp = R(0), sm = R(0);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) {
-            sp += L[c] * dfp[c * cells + ep];
-            sm += L[c] * dfm[c * cells + em];
-          }
-          dp[i] = sp;
-          dm[i] = -sm;
-        }
         R tol = R(0);
         if constexpr (FP32) {
           R ln = R(0);
@@ -584,36 +568,43 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
           tol = R(1 << ORDER) * FLT_EPSILON * ln * M;
         }
-        int ip, im;
-        bool mp = false, mm = false;
-        R cp = eno_select<ORDER, R, FP32>(dp, delta, tie_rel, tol, ip, mp);
-        R cm = eno_select<ORDER, R, FP32>(dm, delta, tie_rel, tol, im, mm);
-        if constexpr (FP32) {
-          if (mp || mm) {
-            const long long sj = g.s0 + f - 1;
-            if (mp) {
-              ip = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, sj, v, 0, alpha_d);
-              cp = R(0);
+        // f^+ window centred on cell j, then the mirrored f^- window centred
+        // on cell j+1 (d[i] = -(L df^-) at difference j+4-i); one window live
+        // at a time.
+        R cv = R(0);
 #pragma unroll
-              for (int i = GE::LO; i <= GE::HI; ++i) cp += bcoef<R>(ip, i) * dp[i];
-              ++nfall;
-            }
-            if (mm) {
-              im = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, sj, v, 1, alpha_d);
-              cm = R(0);
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          const R* src = sgn == 0 ? dfp : dfm;
+          R d[8];
 #pragma unroll
-              for (int i = GE::LO; i <= GE::HI; ++i) cm += bcoef<R>(im, i) * dm[i];
+          for (int i = 0; i < 8; ++i) d[i] = R(0);
+#pragma unroll
+          for (int i = GE::LO; i <= GE::HI; ++i) {
+            const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+            R acc = R(0);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) acc += L[c] * src[c * cells + e];
+            d[i] = sgn == 0 ? acc : -acc;
+          }
+          int pick;
+          bool marg = false;
+          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, tol, pick, marg);
+          if constexpr (FP32) {
+            if (marg) {
+              pick = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, g.s0 + f - 1, v, sgn, alpha_d);
+              corr = R(0);
+#pragma unroll
+              for (int i = GE::LO; i <= GE::HI; ++i) corr += bcoef<R>(pick, i) * d[i];
               ++nfall;
             }
           }
+          if ((mode & kModeFlux) && A.idx_out && own) {
+            const long long nf = A.ncell / g.nd * (g.nd + 1);
+            const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+            A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
+          }
+          cv += corr;
         }
-        if ((mode & kModeFlux) && A.idx_out && own) {
-          const long long nf = A.ncell / g.nd * (g.nd + 1);
-          const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
-          A.idx_out[(v * 2 + 0) * nf + fc] = (int8_t)ip;
-          A.idx_out[(v * 2 + 1) * nf + fc] = (int8_t)im;
-        }
-        const R cv = cp + cm;
         if constexpr (NV > 1) {
           R Rc[NV];
           right_col<NV, R>(E, v, Rc);
@@ -729,7 +720,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 }
 
 template <int NV, int ORDER, typename R>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs A) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) sweep_kernel(const SweepArgs A) {
   constexpr bool FP32 = sizeof(R) == 4;
   StepState* st = A.st;
   if (st->skip) return;
@@ -739,8 +730,25 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs A) {
   const double dt = st->dt;
   double amax[3] = {0.0, 0.0, 0.0};
   unsigned long long nfall = 0;
-  for (long long tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x)
+  // Dynamic tile queue: tiles differ in cost (FP64 re-decisions cluster at
+  // discontinuities), so blocks pull the next tile instead of striding.  The
+  // last block to leave resets the queue for the next launch on the stream.
+  __shared__ long long s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&st->tile_next, 1ull);
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= A.ntiles) break;
     sweep_tile<NV, ORDER, R>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax, nfall);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1) {
+      st->tile_next = 0ull;
+      st->blocks_done = 0u;
+      __threadfence();
+    }
+  }
 
   if constexpr (FP32) {
     if (nfall) atomicAdd(&st->fallbacks, nfall);

@@ -296,3 +296,36 @@ def test_full_size_2d_workload_sampled_patches():
         r = ref[:, :, y0 - ya:y0 - ya + core, x0 - xa:x0 - xa + core]
         g = got[:, :, y0:y0 + core, x0:x0 + core]
         assert relerr(g, r) <= TOL64, ((x0, y0), relerr(g, r))
+
+
+@pytest.mark.parametrize("precision", [eno.FP64, eno.FP32_BULK])
+def test_results_do_not_depend_on_tiles(precision):
+    # every face is a pure function of its window, so tile shapes and the
+    # order in which blocks take tiles must not change a single bit
+    n = (130, 75)
+    U0 = inputs.euler2d_quadrants(*n, seed=3)
+    outs = []
+    for tiles in (None, ((1, 31), (16, 7)), ((4, 255), (64, 63))):
+        with eno.Solver(n, (0.0, 0.0), (1.0, 1.0), system=eno.EULER, order=5,
+                        precision=precision) as s:
+            if tiles:
+                for d, (ta, ts) in enumerate(tiles):
+                    s.set_tiles(d, ta, ts)
+            s.init_state(U0)
+            s.advance(1e9, cfl=0.5, max_steps=4)
+            outs.append(s.get_state())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_1d_results_do_not_depend_on_tiles_fp32():
+    U0 = inputs.euler1d_riemann(11, seed=100 % 7)
+    outs = []
+    for ts in (127, 255, 31, 15):
+        with eno.Solver((11,), (0.0,), (1.0,), system=eno.EULER, order=5,
+                        precision=eno.FP32_BULK) as s:
+            s.set_tiles(0, 1, ts)
+            s.init_state(U0)
+            s.advance(1e9, cfl=0.5, max_steps=7)
+            outs.append(s.get_state())
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
