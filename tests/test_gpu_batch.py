@@ -44,7 +44,11 @@ def test_batch_equals_single_problem_runs(precision, order):
             s.init_state(U[:, off[i]:off[i + 1]].reshape(3, 1, 1, -1))
             s.advance_steps(nsteps, 0.5)
             ref = s.get_state().reshape(3, -1)
-        assert np.array_equal(got[:, off[i]:off[i + 1]], ref), (i, int(n))
+        # same arithmetic as the single-problem kernel; the two kernels are
+        # compiled separately, so multiply-add contraction may differ by an ulp
+        tol = 1e-12 if precision == eno.FP64 else 1e-7
+        err = np.abs(got[:, off[i]:off[i + 1]] - ref).max() / np.abs(ref).max()
+        assert err <= tol * nsteps, (i, int(n), err)
 
 
 def test_batch_step_matches_oracle():
