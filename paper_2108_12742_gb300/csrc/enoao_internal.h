@@ -90,11 +90,12 @@ cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int*
 
 // Dynamic shared memory of one sweep block: per extended cell, the split
 // differences (2 nv), the face corrections (nv), the Roe ingredients (nv for
-// the Euler equations) and, in FP32 bulk mode, one magnitude bound.
+// the Euler equations) and, in FP32 bulk mode, one magnitude bound and one
+// word of near-tie flags.
 inline size_t sweep_smem_bytes(int nv, int order, int fp32, int ta, int ts) {
   const int G = order / 2 + 2;
   const size_t cells = (size_t)ta * (size_t)(ts + 2 * G);
-  const int per = 3 * nv + (nv > 1 ? nv : 0) + (fp32 ? 1 : 0);
+  const int per = 3 * nv + (nv > 1 ? nv : 0) + (fp32 ? 2 : 0);
   return cells * per * (fp32 ? 4 : 8);
 }
 

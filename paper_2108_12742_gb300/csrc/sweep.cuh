@@ -379,24 +379,13 @@ __device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& 
                                              long long sj, int v, int sign, double alpha) {
   constexpr int G = Geo<ORDER>::G;
   const double gm1 = A.gamma - 1.0;
-  double q[2 * G][NV];
-#pragma unroll
-  for (int k = 0; k < 2 * G; ++k) {
-    const long long s = bc_map(sj - G + 1 + k, g.nd, A.bc);
-    const long long cell = g.base + (g.a0 + a) * g.stride_a + s * g.stride_d;
-    double t[NV];
-    load_state<NV, COHERENT>(A.u_in, A.cstride, cell, A.dir, t);
-#pragma unroll
-    for (int c = 0; c < NV; ++c) q[k][c] = t[c];
-  }
+  const long long line = g.base + (g.a0 + a) * g.stride_a;
+  auto cell_at = [&](long long s) { return line + bc_map(s, g.nd, A.bc) * g.stride_d; };
   double L[NV];
   if constexpr (NV > 1) {
-    double pl[NV], prr[NV], ql[NV], qr[NV];
-#pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      ql[c] = q[G - 1][c];
-      qr[c] = q[G][c];
-    }
+    double ql[NV], qr[NV], pl[NV], prr[NV];
+    load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj), A.dir, ql);
+    load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj + 1), A.dir, qr);
     roe_prims<NV, double>(ql, gm1, pl);
     roe_prims<NV, double>(qr, gm1, prr);
     Eigen<NV, double> E;
@@ -405,25 +394,26 @@ __device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& 
   } else {
     L[0] = 1.0;
   }
-  // projected split differences of the window: k -> difference (k, k+1)
+  // projected split differences of the window, streamed cell by cell:
+  // w[k] is the difference between cells j-G+1+k and j-G+2+k
+  const double sa = sign == 0 ? alpha : -alpha;
   double w[2 * G - 1];
+  double qa[NV];
+  load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj - G + 1), A.dir, qa);
 #pragma unroll
   for (int k = 0; k < 2 * G - 1; ++k) {
-    double qa[NV], qb[NV], dq[NV], dF[NV];
+    double qb[NV], dq[NV], dF[NV];
+    load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj - G + 2 + k), A.dir, qb);
 #pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      qa[c] = q[k][c];
-      qb[c] = q[k + 1][c];
-      dq[c] = qb[c] - qa[c];
-    }
+    for (int c = 0; c < NV; ++c) dq[c] = qb[c] - qa[c];
     flux_diff<NV, double>(qa, qb, dq, gm1, A.adv_speed, dF);
     double acc = 0.0;
 #pragma unroll
-    for (int c = 0; c < NV; ++c)
-      acc += L[c] * (0.5 * (dF[c] + (sign == 0 ? alpha : -alpha) * dq[c]));
+    for (int c = 0; c < NV; ++c) acc += L[c] * (0.5 * (dF[c] + sa * dq[c]));
     w[k] = acc;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) qa[c] = qb[c];
   }
-  // window index k corresponds to difference e = j - G + 1 + k
   double d[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] = 0.0;
@@ -460,7 +450,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   R* dfm = dfp + NV * cells;
   R* Cf = dfm + NV * cells;
   R* prim = Cf + NV * cells;
-  R* mx = prim + NP * cells;  // FP32 only
+  R* mx = prim + NP * cells;                                 // FP32 only
+  unsigned* fixmask = reinterpret_cast<unsigned*>(mx + cells);  // FP32 only
 
   const int dir = A.dir;
   const bool sfast = dir == 0;
@@ -473,6 +464,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const double inv_dx = A.inv_dx;
   auto sidx = [&](int a, int e) { return sfast ? a * SE + e : e * TA + a; };
   (void)TS;
+  // Projected window of face j (extended cells) onto the field with left
+  // eigenvector row L: sign 0 is the f^+ window centred on cell j, sign 1 the
+  // mirrored f^- window centred on cell j+1 (d[i] = -(L df^-) at j+4-i).
+  auto window = [&](int a, int j, int sgn, const R (&L)[NV], R (&d)[8]) {
+    const R* src = sgn == 0 ? dfp : dfm;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = R(0);
+#pragma unroll
+    for (int i = GE::LO; i <= GE::HI; ++i) {
+      const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+      R acc = R(0);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) acc += L[c] * src[c * cells + e];
+      d[i] = sgn == 0 ? acc : -acc;
+    }
+  };
   const int nts = g.nts;
   const int sext = nts + 2 * G;  // extended cells in use
 
@@ -553,6 +560,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       R C[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) C[c] = R(0);
+      unsigned fix = 0;
 #pragma unroll 1
       for (int v = 0; v < NV; ++v) {
         R L[NV];
@@ -568,35 +576,17 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
           tol = R(1 << ORDER) * FLT_EPSILON * ln * M;
         }
-        // f^+ window centred on cell j, then the mirrored f^- window centred
-        // on cell j+1 (d[i] = -(L df^-) at difference j+4-i); one window live
-        // at a time.
+        // f^+ then mirrored f^- window, one live at a time
         R cv = R(0);
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
-          const R* src = sgn == 0 ? dfp : dfm;
           R d[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) d[i] = R(0);
-#pragma unroll
-          for (int i = GE::LO; i <= GE::HI; ++i) {
-            const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
-            R acc = R(0);
-#pragma unroll
-            for (int c = 0; c < NV; ++c) acc += L[c] * src[c * cells + e];
-            d[i] = sgn == 0 ? acc : -acc;
-          }
+          window(a, j, sgn, L, d);
           int pick;
           bool marg = false;
           R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, tol, pick, marg);
           if constexpr (FP32) {
-            if (marg) {
-              pick = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, g.s0 + f - 1, v, sgn, alpha_d);
-              corr = R(0);
-#pragma unroll
-              for (int i = GE::LO; i <= GE::HI; ++i) corr += bcoef<R>(pick, i) * d[i];
-              ++nfall;
-            }
+            if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 in phase 2b
           }
           if ((mode & kModeFlux) && A.idx_out && own) {
             const long long nf = A.ncell / g.nd * (g.nd + 1);
@@ -617,9 +607,83 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       const int sj = sidx(a, j);
 #pragma unroll
       for (int c = 0; c < NV; ++c) Cf[c * cells + sj] = C[c];
+      if constexpr (FP32) fixmask[sj] = fix;
     }
   }
   __syncthreads();
+
+  // ---------------- phase 2b (FP32 bulk): FP64 re-decision of near-ties
+  // Flagged choices are re-decided from the FP64 state, face by face in a
+  // fixed field/sign order, and the face correction is updated by the change
+  // of the chosen value.  Kept out of phase 2 so that the rare FP64 path does
+  // not raise the register footprint of the common one.
+  if constexpr (FP32) {
+    const int cnt = nts + 1;
+    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
+      const int f = sfast ? it % cnt : it / TA;
+      const int a = sfast ? it / cnt : it % TA;
+      if (g.a0 + a >= g.na) continue;
+      const int j = G - 1 + f;
+      const int sj = sidx(a, j);
+      const unsigned fix = fixmask[sj];
+      if (!fix) continue;
+      Eigen<NV, R> E;
+      if constexpr (NV > 1) {
+        R pl[NV], prr[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          pl[c] = prim[c * cells + sidx(a, j)];
+          prr[c] = prim[c * cells + sidx(a, j + 1)];
+        }
+        roe_eigen<NV, R>(pl, prr, gm1, E);
+      }
+      const long long gface = g.s0 + f;
+      const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
+      R dC[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) dC[c] = R(0);
+#pragma unroll 1
+      for (int k = 0; k < 2 * NV; ++k) {
+        if (!(fix & (1u << k))) continue;
+        const int v = k >> 1, sgn = k & 1;
+        R L[NV];
+        if constexpr (NV > 1) {
+          left_row<NV, R>(E, v, L);
+        } else {
+          L[0] = R(1);
+        }
+        R d[8];
+        window(a, j, sgn, L, d);
+        int pick_old;
+        bool m;
+        const R corr_old = eno_select<ORDER, R, false>(d, delta, tie_rel, R(0), pick_old, m);
+        const int pick = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, g.s0 + f - 1, v, sgn, alpha_d);
+        ++nfall;
+        if (pick != pick_old) {
+          R corr = R(0);
+#pragma unroll
+          for (int i = GE::LO; i <= GE::HI; ++i) corr += bcoef<R>(pick, i) * d[i];
+          const R dv = corr - corr_old;
+          if constexpr (NV > 1) {
+            R Rc[NV];
+            right_col<NV, R>(E, v, Rc);
+#pragma unroll
+            for (int c = 0; c < NV; ++c) dC[c] += Rc[c] * dv;
+          } else {
+            dC[0] += dv;
+          }
+        }
+        if ((mode & kModeFlux) && A.idx_out && own) {
+          const long long nf = A.ncell / g.nd * (g.nd + 1);
+          const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+          A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NV; ++c) Cf[c * cells + sj] += dC[c];
+    }
+    __syncthreads();
+  }
 
   // ---------------- phase 3: flux difference and Runge-Kutta combine
   if (mode & kModeFlux) {
@@ -720,7 +784,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 }
 
 template <int NV, int ORDER, typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) sweep_kernel(const SweepArgs A) {
+__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs A) {
   constexpr bool FP32 = sizeof(R) == 4;
   StepState* st = A.st;
   if (st->skip) return;
