@@ -115,7 +115,7 @@ void enoao_destroy(enoao_ctx *ctx);
 
 /* Message of the last failure on this context ("" if none); valid until the
  * next call on the context.  ctx may be NULL (message of the last failed
- * create on this host thread). */
+ * create, or of the last failed enoao_step_noalloc, on this host thread). */
 const char *enoao_last_error(const enoao_ctx *ctx);
 
 /* Sets the state U^n (conserved variables, layout above) and resets time and
@@ -179,6 +179,34 @@ int enoao_launches_per_step(const enoao_ctx *ctx);
  * value.  Errors: ENOAO_EINVAL for shapes the kernels do not support. */
 enoao_status enoao_set_tiles(enoao_ctx *ctx, int dir, int ta, int ts);
 enoao_status enoao_get_tiles(const enoao_ctx *ctx, int dir, int *ta, int *ts);
+
+/* One third-order TVD Runge-Kutta step of a 1D problem that allocates no
+ * device memory.  The paper has no counterpart: this is a deployment aid for
+ * callers that cannot let a library allocate -- applications that reserve
+ * all device memory up front for their own allocator or run under a fixed
+ * memory budget, and time loops that must not pay the implicit device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.
+ *   cfg    : 1D problem (ndim 1, n[0] cells, Euler or scalar advection, order,
+ *            precision, bc[0], gamma / adv_speed, delta, tie_rel as in
+ *            enoao_config); at most 262144 cells -- larger problems return
+ *            ENOAO_EINVAL with a message naming the limit.
+ *   U_in   : device pointer, U^n as [nv][n] float64 (not modified).
+ *   U_out  : device pointer, receives U^{n+1} in the same layout; may equal
+ *            U_in.
+ *   dt     : step size; alpha is computed from U_in (Sec. 2).
+ *   stream : cudaStream_t the work is ordered on (0 = legacy default).
+ * The two intermediate stage states and the step's device-side state live in
+ * one fixed file-scope device array (12 MiB, held on every GPU that loads the
+ * library until the process exits).  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call shares the array and finds the previous
+ * call's contents there (whatever must start at zero is cleared by the call),
+ * so calls that overlap on the GPU -- from other streams or threads -- race:
+ * serialise them.  The call waits for its stream to finish the step and
+ * returns ENOAO_ENONPHYS for rho <= 0, p <= 0 or NaN; messages are read with
+ * enoao_last_error(NULL). */
+enoao_status enoao_step_noalloc(const enoao_config *cfg, const double *U_in, double *U_out,
+                                double dt, void *cuda_stream);
 
 /* Measurement helper: launches the sweep kernel of axis dir for Runge-Kutta
  * stage 0 on the current state nrep times back to back on the library's

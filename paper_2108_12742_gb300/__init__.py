@@ -99,6 +99,7 @@ def load():
         "enoao_autotune": (ctypes.c_int, [P]),
         "enoao_time_sweep": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_float)]),
+        "enoao_step_noalloc": (ctypes.c_int, [C, P, P, ctypes.c_double, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -142,6 +143,21 @@ def make_config(shape, lo, hi, system=EULER, order=5, precision=FP64, bc=TRANSMI
             cfg.n[d], cfg.lo[d], cfg.hi[d], cfg.bc[d] = int(shape[d]), lo[d], hi[d], int(bcs[d])
     cfg.adv_speed, cfg.gamma, cfg.delta, cfg.tie_rel = adv_speed, gamma, delta, tie_rel
     return cfg
+
+
+def step_noalloc(cfg, U_in, U_out, dt, stream=None):
+    """One Runge-Kutta step of a 1D problem through enoao_step_noalloc.
+
+    U_in / U_out are CUDA tensors shaped (nv, n) or (nv, 1, 1, n); the library
+    allocates nothing for the step (its stage states live in a fixed device
+    array of at most 2^18 cells)."""
+    lib = load()
+    pi, di = _ptr(U_in)
+    po, do = _ptr(U_out)
+    assert di and do, "enoao_step_noalloc takes device buffers"
+    st = lib.enoao_step_noalloc(ctypes.byref(cfg), pi, po, dt, _stream_handle(stream))
+    if st:
+        raise EnoaoError(st, lib.enoao_last_error(None).decode())
 
 
 class Solver:

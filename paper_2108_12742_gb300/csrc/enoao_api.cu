@@ -25,6 +25,12 @@ thread_local std::string g_create_error;
 // Batched-problem state (defined with the batch kernels).
 }  // namespace
 
+namespace enoao {
+// Message returned by enoao_last_error(NULL) on this host thread (used by
+// entry points that have no context).
+void set_thread_error(const char* msg) { g_create_error = msg; }
+}  // namespace enoao
+
 namespace {
 
 enoao_status fail(enoao_ctx* c, enoao_status st, const char* fmt, ...) {
