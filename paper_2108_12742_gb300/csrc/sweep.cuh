@@ -138,7 +138,10 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R t
   if constexpr (CHECK) {
     const R tolT = tie_rel * delta + tol_abs;
     bool m = false;
-    if (thr) {
+    if (thr && pick == NC - 1) {
+      // top candidate below the threshold (smooth data): only it decides
+      m = rabs(IS[NC - 1] - delta) <= tolT;
+    } else if (thr) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= tolT);
     } else {
@@ -431,6 +434,30 @@ struct NPrim {
   static constexpr int value = NV > 1 ? NV : 0;
 };
 
+// Runs body(a, e) over the items of a TA x cnt tile, lanes along e for x
+// sweeps (sfast) and along a (the x direction) otherwise, stepping by the
+// block size without an integer division per item.
+template <typename F>
+__device__ __forceinline__ void for_items(int TA, int cnt, bool sfast, F&& body) {
+  const int bd = blockDim.x, tid = threadIdx.x;
+  int a, e, da, de;
+  if (sfast) {
+    e = tid % cnt; a = tid / cnt; de = bd % cnt; da = bd / cnt;
+  } else {
+    a = tid % TA; e = tid / TA; da = bd % TA; de = bd / TA;
+  }
+  while (sfast ? a < TA : e < cnt) {
+    body(a, e);
+    if (sfast) {
+      e += de; a += da;
+      if (e >= cnt) { e -= cnt; ++a; }
+    } else {
+      a += da; e += de;
+      if (a >= TA) { a -= TA; ++e; }
+    }
+  }
+}
+
 // One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
 // constant of the swept axis and the step size; amax accumulates |u_d| + c of
 // combined states (last stage), nfall counts FP64 re-decisions.
@@ -462,7 +489,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const R tie_rel = (R)A.tie_rel;
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
-  auto sidx = [&](int a, int e) { return sfast ? a * SE + e : e * TA + a; };
+  // Shared-memory rows of SE cells per line for every axis: unit stride
+  // along the swept axis (window offsets are immediates); SE is odd, so the
+  // y/z sweeps, whose lanes run across lines, hit distinct banks.
+  auto sidx = [&](int a, int e) { return a * SE + e; };
   (void)TS;
   // Projected window of face j (extended cells) onto the field with left
   // eigenvector row L: sign 0 is the f^+ window centred on cell j, sign 1 the
@@ -486,10 +516,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // ---------------- phase 1: split differences and Roe ingredients
   {
     const int cnt = sext;
-    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-      const int e = sfast ? it % cnt : it / TA;
-      const int a = sfast ? it / cnt : it % TA;
-      if (g.a0 + a >= g.na) continue;
+    for_items(TA, cnt, sfast, [&](const int a, const int e) {
+      if (g.a0 + a >= g.na) return;
       const long long la = g.base + (g.a0 + a) * g.stride_a;
       const long long sa = bc_map(g.s0 - G + e, g.nd, A.bc);
       double qa64[NV];
@@ -528,17 +556,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
         if constexpr (FP32) mx[si] = m;
       }
-    }
+    });
   }
   __syncthreads();
 
   // ---------------- phase 2: per face choice and back-projection
   {
     const int cnt = nts + 1;
-    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-      const int f = sfast ? it % cnt : it / TA;
-      const int a = sfast ? it / cnt : it % TA;
-      if (g.a0 + a >= g.na) continue;
+    for_items(TA, cnt, sfast, [&](const int a, const int f) {
+      if (g.a0 + a >= g.na) return;
       const int j = G - 1 + f;  // face j+1/2 in extended cells
       Eigen<NV, R> E;
       if constexpr (NV > 1) {
@@ -608,7 +634,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
       for (int c = 0; c < NV; ++c) Cf[c * cells + sj] = C[c];
       if constexpr (FP32) fixmask[sj] = fix;
-    }
+    });
   }
   __syncthreads();
 
@@ -619,14 +645,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // not raise the register footprint of the common one.
   if constexpr (FP32) {
     const int cnt = nts + 1;
-    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-      const int f = sfast ? it % cnt : it / TA;
-      const int a = sfast ? it / cnt : it % TA;
-      if (g.a0 + a >= g.na) continue;
+    for_items(TA, cnt, sfast, [&](const int a, const int f) {
+      if (g.a0 + a >= g.na) return;
       const int j = G - 1 + f;
       const int sj = sidx(a, j);
       const unsigned fix = fixmask[sj];
-      if (!fix) continue;
+      if (!fix) return;
       Eigen<NV, R> E;
       if constexpr (NV > 1) {
         R pl[NV], prr[NV];
@@ -681,7 +705,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       }
 #pragma unroll
       for (int c = 0; c < NV; ++c) Cf[c * cells + sj] += dC[c];
-    }
+    });
     __syncthreads();
   }
 
@@ -689,12 +713,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   if (mode & kModeFlux) {
     const int cnt = nts + 1;
     const long long nf = A.ncell / g.nd * (g.nd + 1);
-    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-      const int f = sfast ? it % cnt : it / TA;
-      const int a = sfast ? it / cnt : it % TA;
-      if (g.a0 + a >= g.na) continue;
+    for_items(TA, cnt, sfast, [&](const int a, const int f) {
+      if (g.a0 + a >= g.na) return;
       const long long gface = g.s0 + f;
-      if (!((gface <= g.nd) && (f < A.ts || gface == g.nd))) continue;
+      if (!((gface <= g.nd) && (f < A.ts || gface == g.nd))) return;
       const int j = G - 1 + f;
       const long long la = g.base + (g.a0 + a) * g.stride_a;
       double ql[NV], qr[NV], Fl[NV], Fr[NV];
@@ -709,13 +731,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
         A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + (double)Cf[c * cells + sidx(a, j)];
       }
-    }
+    });
   } else {
     const int cnt = nts;
-    for (int it = threadIdx.x; it < TA * cnt; it += blockDim.x) {
-      const int t = sfast ? it % cnt : it / TA;
-      const int a = sfast ? it / cnt : it % TA;
-      if (g.a0 + a >= g.na) continue;
+    for_items(TA, cnt, sfast, [&](const int a, const int t) {
+      if (g.a0 + a >= g.na) return;
       const int e = G + t;
       const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
       R r[NV];
@@ -732,7 +752,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
           rb[k] = (mode & kModeRhsAdd) ? rb[k] + r[c] : r[c];
         }
-        continue;
+        return;
       }
       double unew[NV];
 #pragma unroll
@@ -778,7 +798,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           atomicMin(&st->err_cell, cell);
         }
       }
-    }
+    });
   }
   __syncthreads();
 }
