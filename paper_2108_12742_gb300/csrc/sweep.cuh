@@ -758,12 +758,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
         const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
-        double Lk;
-        if (mode & kModeRhsAdd) {
-          Lk = (double)(reinterpret_cast<const R*>(A.rhs)[k]) + (double)r[c];
-        } else {
-          Lk = (double)r[c];
-        }
+        // L(u) summed over the axes in the bulk precision, then one rounding
+        // to FP64 for the Runge-Kutta combine
+        R Lsum = r[c];
+        if (mode & kModeRhsAdd) Lsum = reinterpret_cast<const R*>(A.rhs)[k] + r[c];
+        const double Lk = (double)Lsum;
         const double ui = A.u_in[k];
         double un;
         if (A.stage == 0) {
@@ -776,7 +775,38 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         A.u_out[k] = un;
         unew[perm_comp<NV>(c, dir)] = un;  // back in conserved order
       }
-      if constexpr (NV > 1) {
+      if constexpr (FP32) {
+        // FP32 bulk: the state is checked, and the next step's alpha taken,
+        // on each step's final state only; the kinetic energy, sound speed
+        // and |u| + c are FP32, the energy difference E - ke stays FP64.
+        if (A.stage == 2) {
+          if constexpr (NV > 1) {
+            const float rho = (float)unew[0];
+            float m2 = 0.0f;
+#pragma unroll
+            for (int c = 1; c < NV - 1; ++c) {
+              const float m = (float)unew[c];
+              m2 += m * m;
+            }
+            const float ke = 0.5f * m2 / rho;
+            const float p = (float)((A.gamma - 1.0) * (unew[NV - 1] - (double)ke));
+            const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
+            if (!ok) {
+              atomicOr(&st->err, kErrNonPhys);
+              atomicMin(&st->err_cell, cell);
+            } else if (mode & kModeAlpha) {
+              const float ir = 1.0f / rho;
+              const float cs = sqrtf((float)A.gamma * p * ir);
+#pragma unroll
+              for (int d = 0; d < NV - 2; ++d)
+                amax[d] = fmax(amax[d], (double)(fabsf((float)unew[1 + d]) * ir + cs));
+            }
+          } else if (!isfinite(unew[0])) {
+            atomicOr(&st->err, kErrNonPhys);
+            atomicMin(&st->err_cell, cell);
+          }
+        }
+      } else if constexpr (NV > 1) {
         // non-physical check and next-step alpha on the new state
         const double rho = unew[0];
         double m2 = 0.0;
@@ -803,8 +833,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   __syncthreads();
 }
 
+// Minimum resident blocks per SM asked of the compiler for the FP32-bulk
+// sweep (caps its registers at 65536 / (128 * min blocks)).
+#ifndef ENOAO_FP32_MIN_BLOCKS
+#define ENOAO_FP32_MIN_BLOCKS 1
+#endif
+
 template <int NV, int ORDER, typename R>
-__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs A) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? ENOAO_FP32_MIN_BLOCKS : 1)
+    sweep_kernel(const SweepArgs A) {
   constexpr bool FP32 = sizeof(R) == 4;
   StepState* st = A.st;
   if (st->skip) return;
