@@ -212,10 +212,10 @@ void default_tiles(enoao_ctx* c) {
   const bool f32 = fp32(c);
   for (int d = 0; d < c->cfg.ndim; ++d) {
     if (d == 0) {
-      c->ta[d] = c->cfg.ndim == 1 ? 1 : 2;
-      c->ts[d] = f32 ? 127 : 63;
+      c->ta[d] = c->cfg.ndim == 1 ? 1 : 4;
+      c->ts[d] = 63;
     } else {
-      c->ta[d] = 32;
+      c->ta[d] = f32 ? 16 : 32;
       c->ts[d] = f32 ? 31 : 15;
     }
     c->block[d] = 128;
@@ -780,8 +780,8 @@ enoao_status enoao_autotune(enoao_ctx* c) {
   for (int d = 0; d < c->cfg.ndim; ++d) {
     std::vector<std::pair<int, int>> cands;
     if (d == 0) {
-      const int tas[] = {1, 2, 4};
-      const int tss[] = {63, 127, 255};
+      const int tas[] = {1, 2, 4, 8};
+      const int tss[] = {31, 63, 127, 255};
       for (int ta : tas)
         for (int ts : tss)
           if (c->cfg.ndim > 1 || ta == 1) cands.push_back({ta, ts});

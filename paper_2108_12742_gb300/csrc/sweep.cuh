@@ -836,7 +836,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 // Minimum resident blocks per SM asked of the compiler for the FP32-bulk
 // sweep (caps its registers at 65536 / (128 * min blocks)).
 #ifndef ENOAO_FP32_MIN_BLOCKS
-#define ENOAO_FP32_MIN_BLOCKS 1
+#define ENOAO_FP32_MIN_BLOCKS 4
 #endif
 
 template <int NV, int ORDER, typename R>
