@@ -268,6 +268,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
     a.tiles_b = d == 1 ? c->cfg.n[2] : c->cfg.n[1];
   }
   a.ntiles = a.tiles_s * a.tiles_a * a.tiles_b;
+  if (a.ntiles >= (1ll << 31)) return fail(c, ENOAO_EINVAL, "too many tiles for axis %d", d);
   a.inv_dx = 1.0 / c->dx[d];
   a.gamma = c->cfg.gamma;
   a.adv_speed = c->cfg.adv_speed;

@@ -77,10 +77,17 @@ __device__ __forceinline__ double bcoef<double>(int c, int i) { return kB64[c][i
 template <>
 __device__ __forceinline__ float bcoef<float>(int c, int i) { return kB32[c][i]; }
 
+// Absolute value (a sign-bit operation, no floating-point instruction).
+__device__ __forceinline__ double rabs(double a) { return fabs(a); }
+__device__ __forceinline__ float rabs(float a) { return fabsf(a); }
+// Order key of a non-negative value: for doubles the bit pattern read as an
+// integer orders exactly like the value (NaN above everything), so indicator
+// comparisons and minima run on the integer units instead of the FP64 unit,
+// which is 1/64 of the FP32 rate on this part.
+__device__ __forceinline__ long long okey(double a) { return __double_as_longlong(a); }
+__device__ __forceinline__ float okey(float a) { return a; }
 template <typename R>
-__device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
-template <typename R>
-__device__ __forceinline__ R rabs(R a) { return a < R(0) ? -a : a; }
+__device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; }
 
 // ENO-AO choice on one window of first differences d[LO..HI] (d[i] between
 // offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
@@ -107,7 +114,8 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R t
     for (int i = 0; i < 2; ++i) s7[i] = s6[i + 1] - s6[i];
   }
   R IS[9];
-  IS[0] = rmin(R(0.5) * (rabs(d[3]) + rabs(d[2])), R(0.5) * (rabs(d[4]) + rabs(d[5])));
+  // min(a/2, b/2) = min(a, b)/2 exactly (scaling by a power of two)
+  IS[0] = R(0.5) * rmin(rabs(d[3]) + rabs(d[2]), rabs(d[4]) + rabs(d[5]));
   IS[1] = rmin(rabs(s2[3]), rabs(s2[4]));
   IS[2] = rmin(rabs(s3[2]), rabs(s3[3]));
   IS[3] = rmin(rabs(s4[1]), rabs(s4[2]));
@@ -120,9 +128,10 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R t
   }
   // Principle 1: the highest-priority candidate with IS <= delta.
   int pick = -1;
+  const auto kdelta = okey(delta);
 #pragma unroll
   for (int c = 0; c < NC; ++c)
-    if (IS[c] <= delta) pick = c;
+    if (okey(IS[c]) <= kdelta) pick = c;
   const bool thr = pick >= 0;
   // Principle 2: otherwise the smallest IS, equal values to the higher priority.
   R best = IS[0];
@@ -130,7 +139,7 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R t
     pick = 0;
 #pragma unroll
     for (int c = 1; c < NC; ++c)
-      if (IS[c] <= best) {
+      if (okey(IS[c]) <= okey(best)) {
         best = IS[c];
         pick = c;
       }
@@ -320,11 +329,11 @@ __device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[
   }
 }
 
+// Ghost-cell map along the swept axis; s lies within one halo width of
+// [0, n) (n is at least the halo width), so the periodic wrap is one add or
+// subtract -- no integer division, whose 64-bit form runs on the FP64 unit.
 __device__ __forceinline__ long long bc_map(long long s, long long n, int bc) {
-  if (bc == 0) {
-    long long r = s % n;
-    return r < 0 ? r + n : r;
-  }
+  if (bc == 0) return s < 0 ? s + n : (s >= n ? s - n : s);
   return s < 0 ? 0 : (s >= n ? n - 1 : s);
 }
 
@@ -337,10 +346,12 @@ struct TileGeo {
 
 __device__ __forceinline__ TileGeo tile_geo(const SweepArgs& A, long long tile) {
   TileGeo g;
-  const long long ts_i = tile % A.tiles_s;
-  const long long rest = tile / A.tiles_s;
-  const long long ta_i = rest % A.tiles_a;
-  const long long b = rest / A.tiles_a;
+  // tile counts fit 32 bits (checked on the host): 32-bit division only
+  const unsigned t32 = (unsigned)tile, tsn = (unsigned)A.tiles_s, tan = (unsigned)A.tiles_a;
+  const unsigned rest32 = t32 / tsn;
+  const long long ts_i = t32 - rest32 * tsn;
+  const long long b = rest32 / tan;
+  const long long ta_i = rest32 - (unsigned)b * tan;
   const long long n0 = A.n[0], n1 = A.n[1], n2 = A.n[2];
   g.s0 = ts_i * A.ts;
   g.a0 = ta_i * A.ta;
