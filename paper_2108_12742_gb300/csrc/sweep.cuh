@@ -77,6 +77,10 @@ __device__ __forceinline__ double bcoef<double>(int c, int i) { return kB64[c][i
 template <>
 __device__ __forceinline__ float bcoef<float>(int c, int i) { return kB32[c][i]; }
 
+// Square root in the bulk precision (an unqualified sqrt on a float can
+// resolve to the double routine, which runs on the slow FP64 unit).
+__device__ __forceinline__ double bsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float bsqrt(float a) { return sqrtf(a); }
 // Absolute value (a sign-bit operation, no floating-point instruction).
 __device__ __forceinline__ double rabs(double a) { return fabs(a); }
 __device__ __forceinline__ float rabs(float a) { return fabsf(a); }
@@ -246,7 +250,7 @@ __device__ __forceinline__ void roe_prims(const T (&q)[NV], T gm1, T (&pr)[NV]) 
       ke += q[i] * pr[i];
     }
     const T p = gm1 * (q[NV - 1] - T(0.5) * ke);
-    pr[0] = sqrt(q[0]);
+    pr[0] = bsqrt(q[0]);
     pr[NV - 1] = (q[NV - 1] + p) * ir;
   }
 }
@@ -273,7 +277,7 @@ __device__ __forceinline__ void roe_eigen(const T (&pl)[NV], const T (&prr)[NV],
   E.H = wl * pl[NV - 1] + wr * prr[NV - 1];
   E.q2 = q2;
   const T c2 = gm1 * (E.H - T(0.5) * q2);
-  E.c = sqrt(c2);
+  E.c = bsqrt(c2);
   E.ic = T(1) / E.c;
   E.b1 = gm1 / c2;
   E.b2 = T(0.5) * q2 * E.b1;
