@@ -227,6 +227,8 @@ enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
     return fail(c, ENOAO_EINVAL, "tile %dx%d out of range", ta, ts);
   if (d > 0 && ta != 32 && ta != 16 && ta != 64)
     return fail(c, ENOAO_EINVAL, "axis %d needs 16, 32 or 64 lines per tile", d);
+  if (d == 0 && ta != 1 && ta != 2 && ta != 4 && ta != 8)
+    return fail(c, ENOAO_EINVAL, "axis 0 needs 1, 2, 4 or 8 lines per tile");
   size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), ta, ts);
   if (smem > 200 * 1024)
     return fail(c, ENOAO_EINVAL, "tile %dx%d needs %zu bytes of shared memory", ta, ts, smem);

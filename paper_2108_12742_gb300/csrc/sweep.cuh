@@ -449,27 +449,22 @@ struct NPrim {
   static constexpr int value = NV > 1 ? NV : 0;
 };
 
-// Runs body(a, e) over the items of a TA x cnt tile, lanes along e for x
-// sweeps (sfast) and along a (the x direction) otherwise, stepping by the
-// block size without an integer division per item.
+// Runs body(a, e) over the items of a TA x cnt tile.  x sweeps (sfast):
+// each thread keeps one line a and strides along e (lanes along the line);
+// y/z sweeps: each thread keeps one line a (lanes across lines, i.e. along x)
+// and strides along e.  TA is a power of two dividing the block size, so the
+// mapping is shifts and masks -- no per-item integer division.
 template <typename F>
-__device__ __forceinline__ void for_items(int TA, int cnt, bool sfast, F&& body) {
+__device__ __forceinline__ void for_items(int lgTA, int cnt, bool sfast, F&& body) {
   const int bd = blockDim.x, tid = threadIdx.x;
-  int a, e, da, de;
   if (sfast) {
-    e = tid % cnt; a = tid / cnt; de = bd % cnt; da = bd / cnt;
+    const int lgTpl = __ffs(bd) - 1 - lgTA;  // threads per line = bd / TA
+    const int a = tid >> lgTpl, tpl = 1 << lgTpl;
+    for (int e = tid & (tpl - 1); e < cnt; e += tpl) body(a, e);
   } else {
-    a = tid % TA; e = tid / TA; da = bd % TA; de = bd / TA;
-  }
-  while (sfast ? a < TA : e < cnt) {
-    body(a, e);
-    if (sfast) {
-      e += de; a += da;
-      if (e >= cnt) { e -= cnt; ++a; }
-    } else {
-      a += da; e += de;
-      if (a >= TA) { a -= TA; ++e; }
-    }
+    const int a = tid & ((1 << lgTA) - 1);
+    const int step = bd >> lgTA;
+    for (int e = tid >> lgTA; e < cnt; e += step) body(a, e);
   }
 }
 
@@ -508,6 +503,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // along the swept axis (window offsets are immediates); SE is odd, so the
   // y/z sweeps, whose lanes run across lines, hit distinct banks.
   auto sidx = [&](int a, int e) { return a * SE + e; };
+  const int lgTA = __ffs(TA) - 1;  // TA is a power of two (checked on the host)
   (void)TS;
   // Projected window of face j (extended cells) onto the field with left
   // eigenvector row L: sign 0 is the f^+ window centred on cell j, sign 1 the
@@ -531,7 +527,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // ---------------- phase 1: split differences and Roe ingredients
   {
     const int cnt = sext;
-    for_items(TA, cnt, sfast, [&](const int a, const int e) {
+    for_items(lgTA, cnt, sfast, [&](const int a, const int e) {
       if (g.a0 + a >= g.na) return;
       const long long la = g.base + (g.a0 + a) * g.stride_a;
       const long long sa = bc_map(g.s0 - G + e, g.nd, A.bc);
@@ -578,7 +574,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // ---------------- phase 2: per face choice and back-projection
   {
     const int cnt = nts + 1;
-    for_items(TA, cnt, sfast, [&](const int a, const int f) {
+    for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
       if (g.a0 + a >= g.na) return;
       const int j = G - 1 + f;  // face j+1/2 in extended cells
       Eigen<NV, R> E;
@@ -660,7 +656,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // not raise the register footprint of the common one.
   if constexpr (FP32) {
     const int cnt = nts + 1;
-    for_items(TA, cnt, sfast, [&](const int a, const int f) {
+    for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
       if (g.a0 + a >= g.na) return;
       const int j = G - 1 + f;
       const int sj = sidx(a, j);
@@ -728,7 +724,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   if (mode & kModeFlux) {
     const int cnt = nts + 1;
     const long long nf = A.ncell / g.nd * (g.nd + 1);
-    for_items(TA, cnt, sfast, [&](const int a, const int f) {
+    for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
       if (g.a0 + a >= g.na) return;
       const long long gface = g.s0 + f;
       if (!((gface <= g.nd) && (f < A.ts || gface == g.nd))) return;
@@ -749,7 +745,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
     });
   } else {
     const int cnt = nts;
-    for_items(TA, cnt, sfast, [&](const int a, const int t) {
+    for_items(lgTA, cnt, sfast, [&](const int a, const int t) {
       if (g.a0 + a >= g.na) return;
       const int e = G + t;
       const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
