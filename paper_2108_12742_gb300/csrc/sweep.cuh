@@ -81,6 +81,14 @@ __device__ __forceinline__ float bcoef<float>(int c, int i) { return kB32[c][i];
 // resolve to the double routine, which runs on the slow FP64 unit).
 __device__ __forceinline__ double bsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ float bsqrt(float a) { return sqrtf(a); }
+// Reciprocal and quotient in the bulk precision.  FP64 keeps correctly
+// rounded division (parity with the FP64 oracle); the FP32 bulk path uses the
+// fast hardware reciprocal (error of a few ulp, far inside the FP32-bulk
+// tolerance) -- correctly rounded FP32 division is a long routine.
+__device__ __forceinline__ double brcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float brcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double bdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float bdiv(float a, float b) { return __fdividef(a, b); }
 // Absolute value (a sign-bit operation, no floating-point instruction).
 __device__ __forceinline__ double rabs(double a) { return fabs(a); }
 __device__ __forceinline__ float rabs(float a) { return fabsf(a); }
@@ -190,8 +198,8 @@ __device__ __forceinline__ void flux_diff(const T (&qa)[NV], const T (&qb)[NV], 
     dF[0] = adv * dq[0];
   } else {
     constexpr int NT = NV - 3;  // tangential components
-    const T ia = T(1) / qa[0];
-    const T ib = T(1) / qb[0];
+    const T ia = brcp(qa[0]);
+    const T ib = brcp(qb[0]);
     const T u = qa[1] * ia;
     T vt[NT > 0 ? NT : 1], dvt[NT > 0 ? NT : 1];
     const T du = (dq[1] - u * dq[0]) * ib;
@@ -242,7 +250,7 @@ __device__ __forceinline__ void phys_flux(const double (&q)[NV], double gm1, dou
 template <int NV, typename T>
 __device__ __forceinline__ void roe_prims(const T (&q)[NV], T gm1, T (&pr)[NV]) {
   if constexpr (NV > 1) {
-    const T ir = T(1) / q[0];
+    const T ir = brcp(q[0]);
     T ke = T(0);
 #pragma unroll
     for (int i = 1; i < NV - 1; ++i) {
@@ -265,7 +273,7 @@ template <int NV, typename T>
 __device__ __forceinline__ void roe_eigen(const T (&pl)[NV], const T (&prr)[NV], T gm1,
                                           Eigen<NV, T>& E) {
   constexpr int NT = NV - 3;
-  const T inv = T(1) / (pl[0] + prr[0]);
+  const T inv = brcp(pl[0] + prr[0]);
   const T wl = pl[0] * inv, wr = prr[0] * inv;
   E.u = wl * pl[1] + wr * prr[1];
   T q2 = E.u * E.u;
@@ -278,8 +286,8 @@ __device__ __forceinline__ void roe_eigen(const T (&pl)[NV], const T (&prr)[NV],
   E.q2 = q2;
   const T c2 = gm1 * (E.H - T(0.5) * q2);
   E.c = bsqrt(c2);
-  E.ic = T(1) / E.c;
-  E.b1 = gm1 / c2;
+  E.ic = brcp(E.c);
+  E.b1 = bdiv(gm1, c2);
   E.b2 = T(0.5) * q2 * E.b1;
 }
 
@@ -799,14 +807,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
               const float m = (float)unew[c];
               m2 += m * m;
             }
-            const float ke = 0.5f * m2 / rho;
+            const float ke = __fdividef(0.5f * m2, rho);
             const float p = (float)((A.gamma - 1.0) * (unew[NV - 1] - (double)ke));
             const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
             if (!ok) {
               atomicOr(&st->err, kErrNonPhys);
               atomicMin(&st->err_cell, cell);
             } else if (mode & kModeAlpha) {
-              const float ir = 1.0f / rho;
+              const float ir = __fdividef(1.0f, rho);
               const float cs = sqrtf((float)A.gamma * p * ir);
 #pragma unroll
               for (int d = 0; d < NV - 2; ++d)
