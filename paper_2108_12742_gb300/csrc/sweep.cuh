@@ -105,9 +105,15 @@ __device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; 
 // offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
 // CHECK is set, 'marginal' reports a decision that rounding of size tol_abs
 // or a relative gap tie_rel could have changed.
+// Rounding bound of the FP32 bulk indicators: candidate c reads the window
+// differences d[LO_c..HI_c]; mxd[i] bounds the split-flux differences behind
+// d[i], tscale = (NV + 4) eps32 sum|L| turns that into a bound on the error of
+// d[i], and the (m+n)-th difference of d that forms IS_c multiplies it by at
+// most 2^(m+n).  Candidates whose stencil sees only a flat region get a zero
+// bound, so exact zeros next to a jump are not mistaken for near-ties.
 template <int ORDER, typename R, bool CHECK>
-__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R tol_abs,
-                                        int& pick_out, bool& marginal) {
+__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, const R (&mxd)[8],
+                                        R tscale, int& pick_out, bool& marginal) {
   using GE = Geo<ORDER>;
   constexpr int LO = GE::LO, HI = GE::HI, NC = GE::NC;
   R s2[8], s3[8], s4[8], s5[8], s6[8], s7[8];
@@ -157,19 +163,42 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, R t
       }
   }
   if constexpr (CHECK) {
-    const R tolT = tie_rel * delta + tol_abs;
+    // per-candidate bounds from the maxima over each candidate's span
+    R tol[9];
+    const R core = fmaxf(fmaxf(mxd[2], mxd[3]), fmaxf(mxd[4], mxd[5]));  // spans of c0..c2
+    const R m3 = fmaxf(core, mxd[1]);                                   // c3: d[1..5]
+    const R m4 = fmaxf(core, mxd[6]);                                   // c4: d[2..6]
+    const R m5 = fmaxf(m3, mxd[6]);                                     // c5: d[1..6]
+    tol[0] = tscale * core;
+    tol[1] = tscale * R(2) * core;
+    tol[2] = tscale * R(4) * core;
+    tol[3] = tscale * R(8) * m3;
+    tol[4] = tscale * R(8) * m4;
+    tol[5] = tscale * R(16) * m5;
+    if constexpr (ORDER == 7) {
+      const R m6 = fmaxf(m5, mxd[0]);                                   // c6: d[0..6]
+      const R m7 = fmaxf(m5, mxd[7]);                                   // c7: d[1..7]
+      tol[6] = tscale * R(32) * m6;
+      tol[7] = tscale * R(32) * m7;
+      tol[8] = tscale * R(64) * fmaxf(m6, mxd[7]);                      // c8: d[0..7]
+    }
+    const R rel = tie_rel * delta;
     bool m = false;
     if (thr && pick == NC - 1) {
       // top candidate below the threshold (smooth data): only it decides
-      m = rabs(IS[NC - 1] - delta) <= tolT;
+      m = rabs(IS[NC - 1] - delta) <= rel + tol[NC - 1];
     } else if (thr) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= tolT);
+      for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= rel + tol[c]);
     } else {
-      m = (best - delta) <= tolT;
-      const R tolA = tie_rel * best + tol_abs;
+      R tp = tol[0];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) m |= (c != pick) && (IS[c] - best <= tolA);
+      for (int c = 1; c < NC; ++c)
+        if (c == pick) tp = tol[c];
+      m = (best - delta) <= rel + tp;
+      const R relA = tie_rel * best + tp;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m |= (c != pick) && (IS[c] - best <= relA + tol[c]);
     }
     marginal = m;
   }
@@ -448,7 +477,8 @@ __device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& 
     d[i] = sign == 0 ? w[i - 4 + G - 1] : -w[4 - i + G - 1];
   int pick;
   bool m;
-  eno_select<ORDER, double, false>(d, A.delta, 0.0, 0.0, pick, m);
+  const double nomx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  eno_select<ORDER, double, false>(d, A.delta, 0.0, nomx, 0.0, pick, m);
   return pick;
 }
 
@@ -595,11 +625,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
         roe_eigen<NV, R>(pl, prr, gm1, E);
       }
-      R M = R(0);
-      if constexpr (FP32) {
-#pragma unroll
-        for (int e = j - G + 1; e <= j + G - 1; ++e) M = fmaxf(M, mx[sidx(a, e)]);
-      }
       const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
       const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
       R C[NV];
@@ -614,12 +639,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         } else {
           L[0] = R(1);
         }
-        R tol = R(0);
+        R tscale = R(0);
         if constexpr (FP32) {
           R ln = R(0);
 #pragma unroll
           for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
-          tol = R(1 << ORDER) * FLT_EPSILON * ln * M;
+          tscale = R(NV + 4) * FLT_EPSILON * ln;
         }
         // f^+ then mirrored f^- window, one live at a time
         R cv = R(0);
@@ -629,7 +654,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           window(a, j, sgn, L, d);
           int pick;
           bool marg = false;
-          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, tol, pick, marg);
+          R mxd[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) mxd[i] = R(0);
+          if constexpr (FP32) {
+#pragma unroll
+            for (int i = GE::LO; i <= GE::HI; ++i)
+              mxd[i] = mx[sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i)];
+          }
+          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mxd, tscale, pick, marg);
           if constexpr (FP32) {
             if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 in phase 2b
           }
@@ -699,7 +732,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         window(a, j, sgn, L, d);
         int pick_old;
         bool m;
-        const R corr_old = eno_select<ORDER, R, false>(d, delta, tie_rel, R(0), pick_old, m);
+        const R nomx[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        const R corr_old = eno_select<ORDER, R, false>(d, delta, tie_rel, nomx, R(0), pick_old, m);
         const int pick = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, g.s0 + f - 1, v, sgn, alpha_d);
         ++nfall;
         if (pick != pick_old) {
