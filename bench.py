@@ -35,7 +35,7 @@ CFL = 0.5
 SEED = 1
 METRIC = "ENO-AO cell-stage updates/s (FP64 vs FP32-mixed) + L1 err vs FP64 oracle"
 FLOPS_PER_FACE = 885        # FP32 flops of one face of one axis (2D Euler, ENO-AO5)
-BYTES_PER_CELL_X = 32 + 16  # x sweep: read U^(s) (FP64), write L_x (FP32)
+BYTES_PER_CELL_Y = 32 + 16 + 32  # y sweep, stage 0: read U^n (FP64) and L_x (FP32), write U1 (FP64)
 WORKLOAD = "euler2d-4096x4096-quadrant-riemann-ao5"
 
 
@@ -112,12 +112,12 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def profiled_traffic():
+def profiled_traffic(summary):
     """DRAM bytes per launch of the dominant kernel at 4096^2, from the committed
     ncu summary, if that summary was taken on the current kernel source."""
     import hashlib
     import re
-    prof = os.path.join(ROOT, "profiles", "sweep_x_fp32_euler2d.md")
+    prof = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2108_12742_gb300", "csrc", "sweep.cuh")
     if not os.path.exists(prof):
         return None
@@ -278,30 +278,32 @@ def run_gpu(args):
     value = cells * 3 * args.steps / (ms32 / 1e3) * ws
     value64 = cells * 3 * k64 / (ms64 / 1e3) * ws
 
-    # Roofline of the dominant FP32-bulk kernel, the x-axis sweep (largest
-    # share of the step in the launch list).  It is timed alone right after
-    # the timed region on the library's stream (CUDA events on that stream),
-    # stage 0 in the mode it has inside a step (stores L_x(u) for the y sweep).
-    # Algorithmic work per face of that launch (2D Euler, ENO-AO5): 885 FP32
-    # flops; algorithmic bytes per cell: read U (4 x 8 B), write L_x (4 x 4 B).
+    # Roofline of the dominant FP32-bulk kernel, the y-axis sweep (largest
+    # share of a step in the launch list): it adds L_x, combines and, on the
+    # last stage, checks the state and takes the next alpha.  It is timed alone
+    # right after the timed region on the library's stream (CUDA events on
+    # that stream), stage 0 in the mode it has inside a step.  Algorithmic
+    # work per face: 885 FP32 flops (2D Euler, ENO-AO5); bytes per cell: read
+    # U^n (4 x 8 B) and L_x (4 x 4 B), write U1 (4 x 8 B).
     peaks, peak_kind = measured_peaks()
-    dom = 0
+    dom = 1
     t_dom = k_ms32[dom] / 1e3
     props = torch.cuda.get_device_properties(local)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     flops = FLOPS_PER_FACE * cells
     achieved = flops / t_dom / 1e12
-    traffic = profiled_traffic()
+    traffic = profiled_traffic("sweep_y_fp32_euler2d.md")
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
-                "kernel": "sweep_kernel<4,5,float> x axis (stage 0, stores L_x)",
+                "kernel": "sweep_kernel<4,5,float> y axis (stage 0, adds L_x, combines)",
                 "peak_kind": "FP32 lanes x clock (%d SMs x 128 x 2 flop x %.0f MHz)"
                              % (props.multi_processor_count, sm_mhz),
                 "kernel_ms": k_ms32[dom], "algorithmic_flops_per_launch": flops,
-                "hbm": {"achieved": BYTES_PER_CELL_X * cells / t_dom / 1e9,
+                "hbm": {"achieved": BYTES_PER_CELL_Y * cells / t_dom / 1e9,
                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": BYTES_PER_CELL_X * cells / t_dom / 1e9 / peaks["hbm_gbs"],
+                        "frac": BYTES_PER_CELL_Y * cells / t_dom / 1e9 / peaks["hbm_gbs"],
+                        "algorithmic_bytes_per_launch": BYTES_PER_CELL_Y * cells,
                         "peak_kind": peak_kind}}
 
     launches = (s32.launches_per_step() * args.steps) if rank == 0 else 0
