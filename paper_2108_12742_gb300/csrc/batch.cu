@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
     A.bc = B.bc;
     A.ta = 1;
     A.ts = B.ts;
+    A.se = B.ts + 2 * Geo<ORDER>::G;  // sweep_row_pitch of a one-line x tile
     A.tiles_s = (n + B.ts - 1) / B.ts;
     A.tiles_a = A.tiles_b = 1;
     A.ntiles = A.tiles_s;
@@ -262,7 +263,8 @@ BatchArgs make_args(enoao_ctx* c, int nsteps, double cfl) {
 enoao_status enqueue_batch(enoao_ctx* c, int nsteps, double cfl) {
   BatchState* b = c->batch;
   const int f32 = c->cfg.precision == ENOAO_FP32_BULK;
-  const size_t smem = sweep_smem_bytes(b->nv, c->cfg.order, f32, 1, b->ts);
+  const size_t smem = sweep_smem_bytes(b->nv, c->cfg.order, f32, 1, b->ts,
+                                       sweep_row_pitch(c->cfg.order, f32, 0, 1, b->ts));
   cudaError_t e = launch_batch(b->nv, c->cfg.order, f32, make_args(c, nsteps, cfl), b->block, smem,
                                c->sms, c->s);
   if (e != cudaSuccess)

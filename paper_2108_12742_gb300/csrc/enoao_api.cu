@@ -229,7 +229,8 @@ enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
     return fail(c, ENOAO_EINVAL, "axis %d needs 16, 32 or 64 lines per tile", d);
   if (d == 0 && ta != 1 && ta != 2 && ta != 4 && ta != 8)
     return fail(c, ENOAO_EINVAL, "axis 0 needs 1, 2, 4 or 8 lines per tile");
-  size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), ta, ts);
+  size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), ta, ts,
+                                 sweep_row_pitch(c->cfg.order, fp32(c), d, ta, ts));
   if (smem > 200 * 1024)
     return fail(c, ENOAO_EINVAL, "tile %dx%d needs %zu bytes of shared memory", ta, ts, smem);
   return ENOAO_OK;
@@ -259,6 +260,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.stage = stage;
   a.ta = c->ta[d];
   a.ts = c->ts[d];
+  a.se = sweep_row_pitch(c->cfg.order, fp32(c), d, a.ta, a.ts);
   const long long nd = c->cfg.n[d];
   a.tiles_s = (nd + a.ts - 1) / a.ts;
   if (d == 0) {
@@ -276,7 +278,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.adv_speed = c->cfg.adv_speed;
   a.delta = c->cfg.delta;
   a.tie_rel = c->cfg.tie_rel;
-  const size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts);
+  const size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts, a.se);
   const int block = c->block[d];
   int per_sm = 1;
   cudaError_t e;

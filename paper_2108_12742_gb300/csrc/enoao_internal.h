@@ -62,6 +62,8 @@ struct SweepArgs {
   int mode;
   int stage;            // Runge-Kutta stage 0..2
   int ta, ts;           // tile: lines x faces
+  int se;               // shared-memory row pitch in cells (sweep_row_pitch)
+  int pad_se;
   long long tiles_s;    // tiles along dir
   long long tiles_a;    // tiles across the line index
   long long tiles_b;    // tiles along the remaining axis (dir != 0)
@@ -92,9 +94,26 @@ cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int*
 // differences (2 nv), the face corrections (nv), the Roe ingredients (nv for
 // the Euler equations) and, in FP32 bulk mode, one magnitude bound and one
 // word of near-tie flags.
-inline size_t sweep_smem_bytes(int nv, int order, int fp32, int ta, int ts) {
+// Row pitch (cells) of a tile's shared-memory rows.  x sweeps read along a
+// row (any pitch); y/z sweeps put lines on lanes, so the pitch must spread a
+// warp's lanes over distinct banks: odd for 32- and 64-line tiles and for
+// 8-byte elements, 2 (mod 4) for 16-line FP32 tiles (a warp then spans two
+// cells of 16 lines).
+inline int sweep_row_pitch(int order, int fp32, int dir, int ta, int ts) {
   const int G = order / 2 + 2;
-  const size_t cells = (size_t)ta * (size_t)(ts + 2 * G);
+  int se = ts + 2 * G;
+  if (dir == 0) return se;
+  if (fp32 && ta == 16) {
+    while (se % 4 != 2) ++se;
+  } else {
+    if (se % 2 == 0) ++se;
+  }
+  return se;
+}
+
+inline size_t sweep_smem_bytes(int nv, int order, int fp32, int ta, int ts, int se) {
+  (void)ts;
+  const size_t cells = (size_t)ta * (size_t)se;
   const int per = 3 * nv + (nv > 1 ? nv : 0) + (fp32 ? 2 : 0);
   return cells * per * (fp32 ? 4 : 8);
 }

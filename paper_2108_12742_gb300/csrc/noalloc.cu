@@ -159,6 +159,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   a.bc = cfg->bc[0];
   a.ta = 1;
   a.ts = f32 ? 127 : 63;
+  a.se = sweep_row_pitch(cfg->order, f32, 0, a.ta, a.ts);
   a.tiles_s = (n + a.ts - 1) / a.ts;
   a.tiles_a = a.tiles_b = 1;
   a.ntiles = a.tiles_s;
@@ -167,7 +168,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   a.adv_speed = cfg->adv_speed;
   a.delta = cfg->delta;
   a.tie_rel = cfg->tie_rel;
-  const size_t smem = sweep_smem_bytes(nv, cfg->order, f32, a.ta, a.ts);
+  const size_t smem = sweep_smem_bytes(nv, cfg->order, f32, a.ta, a.ts, a.se);
   const int block = 128;
   int per_sm = 1;
   e = f32 ? sweep_configure_fp32(nv, cfg->order, smem) : sweep_configure_fp64(nv, cfg->order, smem);

@@ -427,20 +427,32 @@ __device__ __forceinline__ void load_state(const double* __restrict__ U, long lo
   }
 }
 
-// FP64 re-decision of one FP32 choice: rebuilds the projected window of face
-// j+1/2 (global cell index sj of cell j along the line) from the FP64 state.
-template <int NV, int ORDER, bool COHERENT>
-__device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& g, int a,
-                                             long long sj, int v, int sign, double alpha) {
+// Lane group of W lanes (a power of two, at least the 2G window cells) that
+// re-decides one choice in FP64 together: lane r holds window cell r, forms
+// difference r with its neighbour's state, and the projected window is then
+// gathered by shuffles; every lane of the group returns the same pick.  Groups
+// of the same warp work on different choices at the same time, so the FP64
+// unit (1/64 of the FP32 rate) runs on full warps instead of single lanes.
+template <int NV, int ORDER, bool COHERENT, int W>
+__device__ __forceinline__ int redo_group(const SweepArgs& A, const TileGeo& g, int a,
+                                          long long sj, int v, int sgn, double alpha, int r) {
   constexpr int G = Geo<ORDER>::G;
+  static_assert(W >= 2 * G, "a lane per window cell");
+  const unsigned FULL = 0xffffffffu;
   const double gm1 = A.gamma - 1.0;
   const long long line = g.base + (g.a0 + a) * g.stride_a;
-  auto cell_at = [&](long long s) { return line + bc_map(s, g.nd, A.bc) * g.stride_d; };
+  const int rr = r < 2 * G ? r : 2 * G - 1;
+  double q[NV];
+  load_state<NV, COHERENT>(A.u_in, A.cstride, line + bc_map(sj - G + 1 + rr, g.nd, A.bc) * g.stride_d,
+                           A.dir, q);
   double L[NV];
   if constexpr (NV > 1) {
     double ql[NV], qr[NV], pl[NV], prr[NV];
-    load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj), A.dir, ql);
-    load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj + 1), A.dir, qr);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      ql[c] = __shfl_sync(FULL, q[c], G - 1, W);
+      qr[c] = __shfl_sync(FULL, q[c], G, W);
+    }
     roe_prims<NV, double>(ql, gm1, pl);
     roe_prims<NV, double>(qr, gm1, prr);
     Eigen<NV, double> E;
@@ -449,37 +461,40 @@ __device__ __noinline__ int redo_choice_fp64(const SweepArgs& A, const TileGeo& 
   } else {
     L[0] = 1.0;
   }
-  // projected split differences of the window, streamed cell by cell:
-  // w[k] is the difference between cells j-G+1+k and j-G+2+k
-  const double sa = sign == 0 ? alpha : -alpha;
-  double w[2 * G - 1];
-  double qa[NV];
-  load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj - G + 1), A.dir, qa);
+  double qn[NV];
 #pragma unroll
-  for (int k = 0; k < 2 * G - 1; ++k) {
-    double qb[NV], dq[NV], dF[NV];
-    load_state<NV, COHERENT>(A.u_in, A.cstride, cell_at(sj - G + 2 + k), A.dir, qb);
+  for (int c = 0; c < NV; ++c) qn[c] = __shfl_down_sync(FULL, q[c], 1, W);
+  double w = 0.0;
+  {
+    double dq[NV], dF[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) dq[c] = qb[c] - qa[c];
-    flux_diff<NV, double>(qa, qb, dq, gm1, A.adv_speed, dF);
-    double acc = 0.0;
+    for (int c = 0; c < NV; ++c) dq[c] = qn[c] - q[c];
+    flux_diff<NV, double>(q, qn, dq, gm1, A.adv_speed, dF);
+    const double sa = sgn == 0 ? alpha : -alpha;
 #pragma unroll
-    for (int c = 0; c < NV; ++c) acc += L[c] * (0.5 * (dF[c] + sa * dq[c]));
-    w[k] = acc;
-#pragma unroll
-    for (int c = 0; c < NV; ++c) qa[c] = qb[c];
+    for (int c = 0; c < NV; ++c) w += L[c] * (0.5 * (dF[c] + sa * dq[c]));
   }
+  // window difference k (between cells k and k+1) sits in group lane k
   double d[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] = 0.0;
 #pragma unroll
-  for (int i = Geo<ORDER>::LO; i <= Geo<ORDER>::HI; ++i)
-    d[i] = sign == 0 ? w[i - 4 + G - 1] : -w[4 - i + G - 1];
+  for (int i = Geo<ORDER>::LO; i <= Geo<ORDER>::HI; ++i) {
+    const int k = sgn == 0 ? i - 4 + G - 1 : 4 - i + G - 1;
+    const double wk = __shfl_sync(FULL, w, k, W);
+    d[i] = sgn == 0 ? wk : -wk;
+  }
   int pick;
   bool m;
   const double nomx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   eno_select<ORDER, double, false>(d, A.delta, 0.0, nomx, 0.0, pick, m);
   return pick;
+}
+
+// Position of the n-th (0-based) set bit of x, or -1.
+__device__ __forceinline__ int nth_set_bit(unsigned x, int n) {
+  for (int i = 0; i < n && x; ++i) x &= x - 1;
+  return x ? __ffs(x) - 1 : -1;
 }
 
 template <int NV>
@@ -519,7 +534,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   constexpr int NP = NPrim<NV>::value;
   StepState* st = A.st;
   const int TA = A.ta, TS = A.ts;
-  const int SE = TS + 2 * G;
+  const int SE = A.se;  // row pitch (>= TS + 2G), chosen on the host for conflict-free banks
   const int cells = TA * SE;
   R* dfp = reinterpret_cast<R*>(smem_raw);
   R* dfm = dfp + NV * cells;
@@ -691,25 +706,65 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   __syncthreads();
 
   // ---------------- phase 2b (FP32 bulk): FP64 re-decision of near-ties
-  // Flagged choices are re-decided from the FP64 state, face by face in a
-  // fixed field/sign order, and the face correction is updated by the change
-  // of the chosen value.  Kept out of phase 2 so that the rare FP64 path does
-  // not raise the register footprint of the common one.
+  // Flagged choices are re-decided from the FP64 state by lane groups of the
+  // warp (redo_group), then each face applies the changes of its chosen values
+  // to its correction in a fixed field/sign order.  Kept out of phase 2 so the
+  // rare FP64 path does not raise the register footprint of the common one.
   if constexpr (FP32) {
+    constexpr int W = 2 * G <= 8 ? 8 : 16;  // lanes per re-decision group
+    const unsigned FULL = 0xffffffffu;
     const int cnt = nts + 1;
-    for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
-      if (g.a0 + a >= g.na) return;
+    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    int al, e0, estep;  // this thread's line, first face and face stride (as for_items)
+    if (sfast) {
+      const int lgTpl = __ffs(bd) - 1 - lgTA;
+      al = tid >> lgTpl;
+      e0 = tid & ((1 << lgTpl) - 1);
+      estep = 1 << lgTpl;
+    } else {
+      al = tid & (TA - 1);
+      e0 = tid >> lgTA;
+      estep = bd >> lgTA;
+    }
+    const int rounds = (cnt + estep - 1) / estep;  // the same for every lane
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int f = e0 + rd * estep;
+      const bool valid = f < cnt && g.a0 + al < g.na;
       const int j = G - 1 + f;
-      const int sj = sidx(a, j);
-      const unsigned fix = fixmask[sj];
-      if (!fix) return;
+      const unsigned fix = valid ? fixmask[sidx(al, j)] : 0u;
+      if (!__any_sync(FULL, fix != 0u)) continue;
+      // re-decide every flagged choice of the warp, one per group per pass
+      unsigned todo = fix;
+      unsigned long long picks = 0ull;
+      for (;;) {
+        const unsigned have = __ballot_sync(FULL, todo != 0u);
+        if (!have) break;
+        const int src = nth_set_bit(have, lane / W);
+        const int srcl = src < 0 ? 0 : src;
+        const int k = __shfl_sync(FULL, todo ? __ffs(todo) - 1 : 0, srcl);
+        int ga = __shfl_sync(FULL, al, srcl);
+        int gf = __shfl_sync(FULL, f, srcl);
+        if (src < 0) {  // idle group: a valid face of the tile, result unused
+          ga = 0;
+          gf = 0;
+        }
+        const int pick = redo_group<NV, ORDER, COHERENT, W>(A, g, ga, g.s0 + gf - 1, k >> 1, k & 1,
+                                                            alpha_d, lane & (W - 1));
+        if (lane == src) {
+          todo &= ~(1u << k);
+          picks |= (unsigned long long)pick << (4 * k);
+          ++nfall;
+        }
+      }
+      if (!fix) continue;
+      // apply the changed choices of this face
       Eigen<NV, R> E;
       if constexpr (NV > 1) {
         R pl[NV], prr[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          pl[c] = prim[c * cells + sidx(a, j)];
-          prr[c] = prim[c * cells + sidx(a, j + 1)];
+          pl[c] = prim[c * cells + sidx(al, j)];
+          prr[c] = prim[c * cells + sidx(al, j + 1)];
         }
         roe_eigen<NV, R>(pl, prr, gm1, E);
       }
@@ -722,6 +777,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       for (int k = 0; k < 2 * NV; ++k) {
         if (!(fix & (1u << k))) continue;
         const int v = k >> 1, sgn = k & 1;
+        const int pick = (int)((picks >> (4 * k)) & 15ull);
         R L[NV];
         if constexpr (NV > 1) {
           left_row<NV, R>(E, v, L);
@@ -729,13 +785,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           L[0] = R(1);
         }
         R d[8];
-        window(a, j, sgn, L, d);
+        window(al, j, sgn, L, d);
         int pick_old;
         bool m;
         const R nomx[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
         const R corr_old = eno_select<ORDER, R, false>(d, delta, tie_rel, nomx, R(0), pick_old, m);
-        const int pick = redo_choice_fp64<NV, ORDER, COHERENT>(A, g, a, g.s0 + f - 1, v, sgn, alpha_d);
-        ++nfall;
         if (pick != pick_old) {
           R corr = R(0);
 #pragma unroll
@@ -752,13 +806,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
         if ((mode & kModeFlux) && A.idx_out && own) {
           const long long nf = A.ncell / g.nd * (g.nd + 1);
-          const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+          const long long fc = g.fbase + (g.a0 + al) * g.fstride_a + gface * g.fstride_d;
           A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
         }
       }
+      const int sj = sidx(al, j);
 #pragma unroll
       for (int c = 0; c < NV; ++c) Cf[c * cells + sj] += dC[c];
-    });
+    }
     __syncthreads();
   }
 
