@@ -733,12 +733,21 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       const int j = G - 1 + f;
       const unsigned fix = valid ? fixmask[sidx(al, j)] : 0u;
       if (!__any_sync(FULL, fix != 0u)) continue;
-      // re-decide every flagged choice of the warp, one per group per pass
+      // Re-decide every flagged choice of the warp: in each pass, group gi
+      // takes the lowest flagged choice of the gi-th lane that still has one,
+      // and that lane collects the result from group gi.  Every pass clears at
+      // least one of the at most 32 * 2 NV flags, so the pass bound is never
+      // reached; if it were, the error word says so.
+      constexpr int NG = 32 / W;
       unsigned todo = fix;
       unsigned long long picks = 0ull;
-      for (;;) {
+      for (int pass = 0; pass < 64 * NV + 1; ++pass) {
         const unsigned have = __ballot_sync(FULL, todo != 0u);
         if (!have) break;
+        if (pass == 64 * NV) {
+          if (lane == 0) atomicOr(&st->err, kErrTimeout);
+          break;
+        }
         const int src = nth_set_bit(have, lane / W);
         const int srcl = src < 0 ? 0 : src;
         const int k = __shfl_sync(FULL, todo ? __ffs(todo) - 1 : 0, srcl);
@@ -750,9 +759,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
         const int pick = redo_group<NV, ORDER, COHERENT, W>(A, g, ga, g.s0 + gf - 1, k >> 1, k & 1,
                                                             alpha_d, lane & (W - 1));
-        if (lane == src) {
-          todo &= ~(1u << k);
-          picks |= (unsigned long long)pick << (4 * k);
+        // my rank among the lanes with work tells which group (if any) took it
+        const int rank = __popc(have & ((1u << lane) - 1u));
+        const int mine = __shfl_sync(FULL, pick, (rank < NG ? rank : 0) * W);
+        if (todo != 0u && rank < NG) {
+          const int kk = __ffs(todo) - 1;
+          todo &= ~(1u << kk);
+          picks |= (unsigned long long)mine << (4 * kk);
           ++nfall;
         }
       }
