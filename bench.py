@@ -344,6 +344,153 @@ def run_gpu(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# Further workloads (not the headline line): python bench.py --workload NAME
+# ----------------------------------------------------------------------------
+def _line(workload, value, ms_step, steps, warmup, extra):
+    d = {"metric": METRIC, "value": value, "unit": "cell-stage updates/s", "n_gpus": 1,
+         "steps": steps, "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True,
+         "scaling": "weak", "vs_baseline": None, "dtype": "f32-bulk/f64-state",
+         "data": "synthetic", "config": {"workload": workload}}
+    d.update(extra)
+    print(json.dumps(d))
+
+
+def _timed_steps(s, k, warmup, cfl, stream):
+    import torch
+    s.advance_steps(warmup, cfl)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.advance_steps_async(k, cfl)
+    e1.record(stream)
+    s.sync()
+    return e0.elapsed_time(e1)
+
+
+def run_batched(args):
+    """4096 independent 1D Euler problems, N ~ log-uniform[256, 16384], 200 steps
+    in one persistent launch (FP32 bulk and FP64), against one launch per problem
+    (timed on a random subset of the problems, scaled by their cells)."""
+    import torch
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    nprob, nsteps = 4096, args.batch_steps
+    sizes = inputs.batch_sizes(nprob, seed=2024)
+    U = inputs.batch_states(sizes, seed=10_000)
+    cells = int(sizes.sum())
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
+        with eno.Batch(sizes, 0.0, 1.0, stream=stream, system=eno.EULER, order=5,
+                       precision=prec) as b:
+            b.init_state(U)
+            b.autotune()
+            b.init_state(U)
+            b.advance_steps(1, CFL)          # warm-up launch
+            b.init_state(U)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.advance_steps_async(nsteps, CFL)
+            e1.record(stream)
+            b.sync()
+            ms = e0.elapsed_time(e1)
+            res[name] = {"value": cells * 3 * nsteps / (ms / 1e3), "ms_total": ms,
+                         "state": b.get_state()}
+    # one launch per problem: the single-problem path on a seeded subset
+    rng = np.random.default_rng(7)
+    sub = np.sort(rng.choice(nprob, size=args.batch_subset, replace=False))
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    ms_sub, cells_sub = 0.0, 0
+    for i in sub:
+        n = int(sizes[i])
+        with eno.Solver((n,), (0.0,), (1.0,), stream=stream, system=eno.EULER, order=5,
+                        precision=eno.FP32_BULK) as s:
+            s.init_state(U[:, off[i]:off[i + 1]].reshape(3, 1, 1, n))
+            ms_sub += _timed_steps(s, nsteps, 0, CFL, stream)
+            cells_sub += n
+    per_problem = cells_sub * 3 * nsteps / (ms_sub / 1e3)
+    a, b = res["fp32_bulk"]["state"], res["fp64"]["state"]
+    l1 = [float(np.abs(a[v] - b[v]).mean() / np.abs(b[v]).mean()) for v in range(3)]
+    _line("batched-euler1d-4096-problems-N256-16384-ao5", res["fp32_bulk"]["value"],
+          res["fp32_bulk"]["ms_total"] / nsteps, nsteps, 1,
+          {"config": {"workload": "batched-euler1d-4096-problems-N256-16384-ao5", "cells": cells,
+                      "problems": nprob, "steps_per_launch": nsteps, "launches": 1},
+           "fp64": {"value": res["fp64"]["value"], "ms_total": res["fp64"]["ms_total"]},
+           "fp32_bulk_speedup_vs_fp64": res["fp32_bulk"]["value"] / res["fp64"]["value"],
+           "one_launch_per_problem": {"value": per_problem, "problems_timed": len(sub),
+                                      "cells_timed": cells_sub,
+                                      "note": "single-problem path, FP32 bulk, same steps"},
+           "batched_speedup_vs_per_problem": res["fp32_bulk"]["value"] / per_problem,
+           "l1_rel_fp32_bulk_vs_fp64": l1})
+
+
+def run_euler3d(args):
+    """3D Euler 512^3, periodic, ENO-AO7: FP32 bulk vs FP64 (a few steps)."""
+    import torch
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    n = args.n3d
+    U = torch.from_numpy(inputs.euler3d_blast(n, seed=1)).cuda()
+    cells = n ** 3
+    stream = torch.cuda.current_stream()
+    out = {}
+    states = {}
+    for name, prec, k in (("fp32_bulk", eno.FP32_BULK, args.steps3d), ("fp64", eno.FP64, 1)):
+        with eno.Solver((n, n, n), (0.0,) * 3, (1.0,) * 3, stream=stream, system=eno.EULER,
+                        order=7, bc=eno.PERIODIC, precision=prec) as s:
+            s.init_state(U)
+            ms = _timed_steps(s, k, 1, CFL, stream)
+            kms = [s.time_sweep(d, 2) for d in range(3)]
+            s.init_state(U)
+            s.advance_steps(1, CFL)
+            st = torch.empty_like(U)
+            s.get_state(st)
+            states[name] = st
+            out[name] = {"value": cells * 3 * k / (ms / 1e3), "ms_per_step": ms / k, "steps": k,
+                         "kernel_ms": kms}
+    diff = (states["fp32_bulk"] - states["fp64"]).abs()
+    l1 = [float(diff[v].mean() / states["fp64"][v].abs().mean()) for v in range(5)]
+    linf = [float(diff[v].max() / states["fp64"][v].abs().max()) for v in range(5)]
+    _line(f"euler3d-{n}^3-periodic-blast-ao7", out["fp32_bulk"]["value"],
+          out["fp32_bulk"]["ms_per_step"], out["fp32_bulk"]["steps"], 1,
+          {"config": {"workload": f"euler3d-{n}^3-periodic-blast-ao7", "cells": cells, "order": 7},
+           "fp64": out["fp64"], "kernel_ms_fp32_bulk": out["fp32_bulk"]["kernel_ms"],
+           "fp32_bulk_speedup_vs_fp64": out["fp32_bulk"]["value"] / out["fp64"]["value"],
+           "l1_rel_fp32_bulk_vs_fp64_one_step": l1, "linf_rel_fp32_bulk_vs_fp64_one_step": linf})
+
+
+def run_small(args, workload):
+    """Launch-bound single problems run to their end time: the 1D Euler Riemann
+    workload (N = 2000, t_end = 0.2) and the periodic advection (N = 200, t = 2)."""
+    import torch
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    if workload == "euler1d":
+        n, t_end, kw = 2000, 0.2, dict(system=eno.EULER, order=5, bc=eno.TRANSMISSIVE)
+        U, lo, hi = inputs.euler1d_riemann(n, seed=1), 0.0, 1.0
+        name = "euler1d-2000-riemann-ao5-to-t0.2"
+    else:
+        n, t_end, kw = 200, 2.0, dict(system=eno.SCALAR_ADVECTION, order=5, bc=eno.PERIODIC)
+        U, lo, hi = inputs.advection_sine(n), -1.0, 1.0
+        name = "advection1d-200-sine-ao5-to-t2"
+    out = {}
+    for pname, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
+        with eno.Solver((n,), (lo,), (hi,), precision=prec, **kw) as s:
+            s.init_state(U)
+            s.advance(t_end, cfl=CFL)       # warm-up run (graph capture)
+            s.init_state(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t, k = s.advance(t_end, cfl=CFL)
+            sec = time.perf_counter() - t0
+            out[pname] = {"value": n * 3 * k / sec, "steps": k, "seconds": sec, "t": t}
+    _line(name, out["fp32_bulk"]["value"], 1e3 * out["fp32_bulk"]["seconds"] / out["fp32_bulk"]["steps"],
+          out["fp32_bulk"]["steps"], 1,
+          {"config": {"workload": name, "cells": n},
+           "fp64": out["fp64"], "note": "launch-bound: whole run timed on the host clock"})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,9 +501,21 @@ def main():
     ap.add_argument("--cpu-sub", type=int, default=1536)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", default="euler2d",
+                    choices=["euler2d", "batched", "euler3d", "euler1d", "advection"])
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-subset", type=int, default=128)
+    ap.add_argument("--n3d", type=int, default=512)
+    ap.add_argument("--steps3d", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "euler3d":
+        return run_euler3d(args)
+    if args.workload in ("euler1d", "advection"):
+        return run_small(args, args.workload)
     return run_gpu(args)
 
 
