@@ -105,15 +105,15 @@ __device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; 
 // offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
 // CHECK is set, 'marginal' reports a decision that rounding of size tol_abs
 // or a relative gap tie_rel could have changed.
-// Rounding bound of the FP32 bulk indicators: candidate c reads the window
-// differences d[LO_c..HI_c]; mxd[i] bounds the split-flux differences behind
-// d[i], tscale = (NV + 4) eps32 sum|L| turns that into a bound on the error of
-// d[i], and the (m+n)-th difference of d that forms IS_c multiplies it by at
-// most 2^(m+n).  Candidates whose stencil sees only a flat region get a zero
-// bound, so exact zeros next to a jump are not mistaken for near-ties.
+// Rounding bound of the FP32 bulk indicators.  e[i] = sum_c |L_c| |df_c| is the
+// magnitude of the terms whose FP32 sum gave d[i], so d[i] carries an error of
+// at most feps * e[i] (feps = (NV + 8) eps32 covers the projection sum and the
+// flux difference behind it).  An undivided difference of d sums its inputs
+// with binomial weights, so the same Pascal sums of e bound its error; IS_c,
+// the smaller of two such differences, is off by at most the larger bound.
 template <int ORDER, typename R, bool CHECK>
-__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, const R (&mxd)[8],
-                                        R tscale, int& pick_out, bool& marginal) {
+__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, const R (&e)[8],
+                                        R feps, int& pick_out, bool& marginal) {
   using GE = Geo<ORDER>;
   constexpr int LO = GE::LO, HI = GE::HI, NC = GE::NC;
   R s2[8], s3[8], s4[8], s5[8], s6[8], s7[8];
@@ -163,24 +163,31 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
       }
   }
   if constexpr (CHECK) {
-    // per-candidate bounds from the maxima over each candidate's span
+    // per-candidate bounds: Pascal sums of e over each indicator's differences
+    R q2[8], q3[8], q4[8], q5[8], q6[8], q7[8];
+#pragma unroll
+    for (int i = LO; i < HI; ++i) q2[i] = e[i] + e[i + 1];
+#pragma unroll
+    for (int i = LO; i < HI - 1; ++i) q3[i] = q2[i] + q2[i + 1];
+#pragma unroll
+    for (int i = LO; i < HI - 2; ++i) q4[i] = q3[i] + q3[i + 1];
+#pragma unroll
+    for (int i = LO; i < HI - 3; ++i) q5[i] = q4[i] + q4[i + 1];
     R tol[9];
-    const R core = fmaxf(fmaxf(mxd[2], mxd[3]), fmaxf(mxd[4], mxd[5]));  // spans of c0..c2
-    const R m3 = fmaxf(core, mxd[1]);                                   // c3: d[1..5]
-    const R m4 = fmaxf(core, mxd[6]);                                   // c4: d[2..6]
-    const R m5 = fmaxf(m3, mxd[6]);                                     // c5: d[1..6]
-    tol[0] = tscale * core;
-    tol[1] = tscale * R(2) * core;
-    tol[2] = tscale * R(4) * core;
-    tol[3] = tscale * R(8) * m3;
-    tol[4] = tscale * R(8) * m4;
-    tol[5] = tscale * R(16) * m5;
+    tol[0] = feps * R(0.5) * fmaxf(e[3] + e[2], e[4] + e[5]);
+    tol[1] = feps * fmaxf(q2[3], q2[4]);
+    tol[2] = feps * fmaxf(q3[2], q3[3]);
+    tol[3] = feps * fmaxf(q4[1], q4[2]);
+    tol[4] = feps * fmaxf(q4[2], q4[3]);
+    tol[5] = feps * fmaxf(q5[1], q5[2]);
     if constexpr (ORDER == 7) {
-      const R m6 = fmaxf(m5, mxd[0]);                                   // c6: d[0..6]
-      const R m7 = fmaxf(m5, mxd[7]);                                   // c7: d[1..7]
-      tol[6] = tscale * R(32) * m6;
-      tol[7] = tscale * R(32) * m7;
-      tol[8] = tscale * R(64) * fmaxf(m6, mxd[7]);                      // c8: d[0..7]
+#pragma unroll
+      for (int i = 0; i < 3; ++i) q6[i] = q5[i] + q5[i + 1];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) q7[i] = q6[i] + q6[i + 1];
+      tol[6] = feps * fmaxf(q6[0], q6[1]);
+      tol[7] = feps * fmaxf(q6[1], q6[2]);
+      tol[8] = feps * fmaxf(q7[0], q7[1]);
     }
     const R rel = tie_rel * delta;
     bool m = false;
@@ -540,8 +547,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   R* dfm = dfp + NV * cells;
   R* Cf = dfm + NV * cells;
   R* prim = Cf + NV * cells;
-  R* mx = prim + NP * cells;                                 // FP32 only
-  unsigned* fixmask = reinterpret_cast<unsigned*>(mx + cells);  // FP32 only
+  // FP32 only: near-tie flags per face (one word per cell slot)
+  unsigned* fixmask = reinterpret_cast<unsigned*>(prim + NP * cells);
 
   const int dir = A.dir;
   const bool sfast = dir == 0;
@@ -572,6 +579,25 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
       for (int c = 0; c < NV; ++c) acc += L[c] * src[c * cells + e];
       d[i] = sgn == 0 ? acc : -acc;
+    }
+  };
+  // the same window with the magnitudes sum_c |L_c| |df_c| of its terms
+  auto window_mag = [&](int a, int j, int sgn, const R (&L)[NV], R (&d)[8], R (&m)[8]) {
+    const R* src = sgn == 0 ? dfp : dfm;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = m[i] = R(0);
+#pragma unroll
+    for (int i = GE::LO; i <= GE::HI; ++i) {
+      const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+      R acc = R(0), mag = R(0);
+#pragma unroll
+      for (int c = 0; c < NV; ++c) {
+        const R x = src[c * cells + e];
+        acc += L[c] * x;
+        mag += rabs(L[c]) * rabs(x);
+      }
+      d[i] = sgn == 0 ? acc : -acc;
+      m[i] = mag;
     }
   };
   const int nts = g.nts;
@@ -609,16 +635,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           dq[c] = (R)(qb64[c] - qa64[c]);
         }
         flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
-        R m = R(0);
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          const R p = R(0.5) * (dF[c] + alpha * dq[c]);
-          const R n = R(0.5) * (dF[c] - alpha * dq[c]);
-          dfp[c * cells + si] = p;
-          dfm[c * cells + si] = n;
-          if constexpr (FP32) m = fmaxf(m, fmaxf(fabsf(p), fabsf(n)));
+          dfp[c * cells + si] = R(0.5) * (dF[c] + alpha * dq[c]);
+          dfm[c * cells + si] = R(0.5) * (dF[c] - alpha * dq[c]);
         }
-        if constexpr (FP32) mx[si] = m;
       }
     });
   }
@@ -654,30 +675,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         } else {
           L[0] = R(1);
         }
-        R tscale = R(0);
-        if constexpr (FP32) {
-          R ln = R(0);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
-          tscale = R(NV + 4) * FLT_EPSILON * ln;
-        }
         // f^+ then mirrored f^- window, one live at a time
         R cv = R(0);
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
-          R d[8];
-          window(a, j, sgn, L, d);
+          R d[8], mag[8];
+          if constexpr (FP32) {
+            window_mag(a, j, sgn, L, d, mag);
+          } else {
+            window(a, j, sgn, L, d);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) mag[i] = R(0);
+          }
           int pick;
           bool marg = false;
-          R mxd[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) mxd[i] = R(0);
-          if constexpr (FP32) {
-#pragma unroll
-            for (int i = GE::LO; i <= GE::HI; ++i)
-              mxd[i] = mx[sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i)];
-          }
-          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mxd, tscale, pick, marg);
+          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
+                                              pick, marg);
           if constexpr (FP32) {
             if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 in phase 2b
           }
