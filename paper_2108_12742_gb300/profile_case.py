@@ -7,7 +7,8 @@ Builds the 2D four-quadrant Euler workload (the benchmark's, at n x n cells;
 (``--ta/--ts``, default: the library's defaults) and launches the sweep
 kernel of axis ``--dir`` nrep times through ``enoao_time_sweep``, printing the
 mean launch time.  The device holds three state buffers and one
-right-hand-side buffer of the chosen size.
+right-hand-side buffer of the chosen size.  ``--steps-before K`` first takes
+K Runge-Kutta steps, so the launches see evolved rather than initial data.
 """
 from __future__ import annotations
 
@@ -27,6 +28,8 @@ def main():
     ap.add_argument("--nrep", type=int, default=2)
     ap.add_argument("--ta", type=int, default=0)
     ap.add_argument("--ts", type=int, default=0)
+    ap.add_argument("--steps-before", type=int, default=0,
+                    help="Runge-Kutta steps taken before the timed launches (evolved data)")
     args = ap.parse_args()
     n = args.n
     prec = eno.FP32_BULK if args.precision == "fp32" else eno.FP64
@@ -40,6 +43,8 @@ def main():
                        bc=eno.PERIODIC, precision=prec)
     with s:
         s.init_state(U)
+        if args.steps_before:
+            s.advance_steps(args.steps_before, 0.5)
         if args.ta or args.ts:
             s.set_tiles(args.dir, args.ta, args.ts)
         ms = s.time_sweep(args.dir, args.nrep)
