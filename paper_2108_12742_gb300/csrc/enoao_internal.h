@@ -92,8 +92,7 @@ cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int*
 
 // Dynamic shared memory of one sweep block: per extended cell, the split
 // differences (2 nv), the face corrections (nv), the Roe ingredients (nv for
-// the Euler equations) and, in FP32 bulk mode, the largest |df| of each
-// difference and one word of near-tie flags.
+// the Euler equations) and, in FP32 bulk mode, one word of near-tie flags.
 // Row pitch (cells) of a tile's shared-memory rows.  x sweeps read along a
 // row (any pitch); y/z sweeps put lines on lanes, so the pitch must spread a
 // warp's lanes over distinct banks: odd for 32- and 64-line tiles and for
@@ -114,7 +113,7 @@ inline int sweep_row_pitch(int order, int fp32, int dir, int ta, int ts) {
 inline size_t sweep_smem_bytes(int nv, int order, int fp32, int ta, int ts, int se) {
   (void)ts;
   const size_t cells = (size_t)ta * (size_t)se;
-  const int per = 3 * nv + (nv > 1 ? nv : 0) + (fp32 ? 2 : 0);
+  const int per = 3 * nv + (nv > 1 ? nv : 0) + (fp32 ? 1 : 0);
   return cells * per * (fp32 ? 4 : 8);
 }
 

@@ -105,13 +105,15 @@ __device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; 
 // offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
 // CHECK is set, 'marginal' reports a decision that rounding of size tol_abs
 // or a relative gap tie_rel could have changed.
-// ENO-AO choice on one window of first differences d[LO..HI] (d[i] between
-// offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre; IS, the
-// pick, whether the threshold principle decided (thr) and the smallest IS
-// (best, argmin regime) are returned for the near-tie test.
-template <int ORDER, typename R>
-__device__ __forceinline__ R eno_core(const R (&d)[8], R delta, R (&IS)[9], int& pick_out,
-                                      bool& thr_out, R& best_out) {
+// Rounding bound of the FP32 bulk indicators.  e[i] = sum_c |L_c| |df_c| is the
+// magnitude of the terms whose FP32 sum gave d[i], so d[i] carries an error of
+// at most feps * e[i] (feps = (NV + 8) eps32 covers the projection sum and the
+// flux difference behind it).  An undivided difference of d sums its inputs
+// with binomial weights, so the same Pascal sums of e bound its error; IS_c,
+// the smaller of two such differences, is off by at most the larger bound.
+template <int ORDER, typename R, bool CHECK>
+__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, const R (&e)[8],
+                                        R feps, int& pick_out, bool& marginal) {
   using GE = Geo<ORDER>;
   constexpr int LO = GE::LO, HI = GE::HI, NC = GE::NC;
   R s2[8], s3[8], s4[8], s5[8], s6[8], s7[8];
@@ -129,6 +131,7 @@ __device__ __forceinline__ R eno_core(const R (&d)[8], R delta, R (&IS)[9], int&
 #pragma unroll
     for (int i = 0; i < 2; ++i) s7[i] = s6[i + 1] - s6[i];
   }
+  R IS[9];
   // min(a/2, b/2) = min(a, b)/2 exactly (scaling by a power of two)
   IS[0] = R(0.5) * rmin(rabs(d[3]) + rabs(d[2]), rabs(d[4]) + rabs(d[5]));
   IS[1] = rmin(rabs(s2[3]), rabs(s2[4]));
@@ -159,83 +162,58 @@ __device__ __forceinline__ R eno_core(const R (&d)[8], R delta, R (&IS)[9], int&
         pick = c;
       }
   }
+  if constexpr (CHECK) {
+    // per-candidate bounds: Pascal sums of e over each indicator's differences
+    R q2[8], q3[8], q4[8], q5[8], q6[8], q7[8];
+#pragma unroll
+    for (int i = LO; i < HI; ++i) q2[i] = e[i] + e[i + 1];
+#pragma unroll
+    for (int i = LO; i < HI - 1; ++i) q3[i] = q2[i] + q2[i + 1];
+#pragma unroll
+    for (int i = LO; i < HI - 2; ++i) q4[i] = q3[i] + q3[i + 1];
+#pragma unroll
+    for (int i = LO; i < HI - 3; ++i) q5[i] = q4[i] + q4[i + 1];
+    R tol[9];
+    tol[0] = feps * R(0.5) * fmaxf(e[3] + e[2], e[4] + e[5]);
+    tol[1] = feps * fmaxf(q2[3], q2[4]);
+    tol[2] = feps * fmaxf(q3[2], q3[3]);
+    tol[3] = feps * fmaxf(q4[1], q4[2]);
+    tol[4] = feps * fmaxf(q4[2], q4[3]);
+    tol[5] = feps * fmaxf(q5[1], q5[2]);
+    if constexpr (ORDER == 7) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) q6[i] = q5[i] + q5[i + 1];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) q7[i] = q6[i] + q6[i + 1];
+      tol[6] = feps * fmaxf(q6[0], q6[1]);
+      tol[7] = feps * fmaxf(q6[1], q6[2]);
+      tol[8] = feps * fmaxf(q7[0], q7[1]);
+    }
+    const R rel = tie_rel * delta;
+    bool m = false;
+    if (thr && pick == NC - 1) {
+      // top candidate below the threshold (smooth data): only it decides
+      m = rabs(IS[NC - 1] - delta) <= rel + tol[NC - 1];
+    } else if (thr) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= rel + tol[c]);
+    } else {
+      R tp = tol[0];
+#pragma unroll
+      for (int c = 1; c < NC; ++c)
+        if (c == pick) tp = tol[c];
+      m = (best - delta) <= rel + tp;
+      const R relA = tie_rel * best + tp;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m |= (c != pick) && (IS[c] - best <= relA + tol[c]);
+    }
+    marginal = m;
+  }
   pick_out = pick;
-  thr_out = thr;
-  best_out = best;
   R corr = R(0);
 #pragma unroll
   for (int i = LO; i <= HI; ++i) corr += bcoef<R>(pick, i) * d[i];
   return corr;
-}
-
-template <int ORDER, typename R>
-__device__ __forceinline__ R eno_select(const R (&d)[8], R delta, int& pick_out) {
-  R IS[9], best;
-  bool thr;
-  return eno_core<ORDER, R>(d, delta, IS, pick_out, thr, best);
-}
-
-// Whether rounding of size tol[c] in IS[c], or a relative gap tie_rel, could
-// change the choice: in the threshold regime any candidate at or above the
-// pick within reach of delta; otherwise the smallest IS within reach of delta
-// or of another candidate.
-template <int ORDER>
-__device__ __forceinline__ bool near_tie(const float (&IS)[9], int pick, bool thr, float best,
-                                         float delta, float tie_rel, const float (&tol)[9]) {
-  constexpr int NC = Geo<ORDER>::NC;
-  const float rel = tie_rel * delta;
-  bool m = false;
-  if (thr && pick == NC - 1) {
-    m = fabsf(IS[NC - 1] - delta) <= rel + tol[NC - 1];
-  } else if (thr) {
-#pragma unroll
-    for (int c = 0; c < NC; ++c) m |= (c >= pick) && (fabsf(IS[c] - delta) <= rel + tol[c]);
-  } else {
-    float tp = tol[0];
-#pragma unroll
-    for (int c = 1; c < NC; ++c)
-      if (c == pick) tp = tol[c];
-    m = (best - delta) <= rel + tp;
-    const float relA = tie_rel * best + tp;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) m |= (c != pick) && (IS[c] - best <= relA + tol[c]);
-  }
-  return m;
-}
-
-// Rounding bound of the FP32 bulk indicators.  e[i] = sum_c |L_c| |df_c| is the
-// magnitude of the terms whose FP32 sum gave d[i], so d[i] carries an error of
-// at most feps * e[i] (feps = (NV + 8) eps32 covers the projection sum and the
-// flux difference behind it).  An undivided difference of d sums its inputs
-// with binomial weights, so the same Pascal sums of e bound its error; IS_c,
-// the smaller of two such differences, is off by at most the larger bound.
-template <int ORDER>
-__device__ __forceinline__ void pascal_tol(const float (&e)[8], float feps, float (&tol)[9]) {
-  constexpr int LO = Geo<ORDER>::LO, HI = Geo<ORDER>::HI;
-  float q2[8], q3[8], q4[8], q5[8], q6[8], q7[8];
-#pragma unroll
-  for (int i = LO; i < HI; ++i) q2[i] = e[i] + e[i + 1];
-#pragma unroll
-  for (int i = LO; i < HI - 1; ++i) q3[i] = q2[i] + q2[i + 1];
-#pragma unroll
-  for (int i = LO; i < HI - 2; ++i) q4[i] = q3[i] + q3[i + 1];
-#pragma unroll
-  for (int i = LO; i < HI - 3; ++i) q5[i] = q4[i] + q4[i + 1];
-  tol[0] = feps * 0.5f * fmaxf(e[3] + e[2], e[4] + e[5]);
-  tol[1] = feps * fmaxf(q2[3], q2[4]);
-  tol[2] = feps * fmaxf(q3[2], q3[3]);
-  tol[3] = feps * fmaxf(q4[1], q4[2]);
-  tol[4] = feps * fmaxf(q4[2], q4[3]);
-  tol[5] = feps * fmaxf(q5[1], q5[2]);
-  if constexpr (ORDER == 7) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) q6[i] = q5[i] + q5[i + 1];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) q7[i] = q6[i] + q6[i + 1];
-    tol[6] = feps * fmaxf(q6[0], q6[1]);
-    tol[7] = feps * fmaxf(q6[1], q6[2]);
-    tol[8] = feps * fmaxf(q7[0], q7[1]);
-  }
 }
 
 // Conserved component stored at position c of the permuted state for a sweep
@@ -514,7 +492,9 @@ __device__ __forceinline__ int redo_group(const SweepArgs& A, const TileGeo& g, 
     d[i] = sgn == 0 ? wk : -wk;
   }
   int pick;
-  eno_select<ORDER, double>(d, A.delta, pick);
+  bool m;
+  const double nomx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  eno_select<ORDER, double, false>(d, A.delta, 0.0, nomx, 0.0, pick, m);
   return pick;
 }
 
@@ -567,9 +547,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   R* dfm = dfp + NV * cells;
   R* Cf = dfm + NV * cells;
   R* prim = Cf + NV * cells;
-  // FP32 only: largest |df| of each difference, and near-tie flags per face
-  R* mx = prim + NP * cells;
-  unsigned* fixmask = reinterpret_cast<unsigned*>(mx + cells);
+  // FP32 only: near-tie flags per face (one word per cell slot)
+  unsigned* fixmask = reinterpret_cast<unsigned*>(prim + NP * cells);
 
   const int dir = A.dir;
   const bool sfast = dir == 0;
@@ -578,7 +557,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const R adv = (R)A.adv_speed;
   const R delta = (R)A.delta;
   const R tie_rel = (R)A.tie_rel;
-  const R feps = R(NV + 8) * R(FLT_EPSILON);  // relative rounding of a projected difference
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
   // Shared-memory rows of SE cells per line for every axis: unit stride
@@ -657,16 +635,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           dq[c] = (R)(qb64[c] - qa64[c]);
         }
         flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
-        R m = R(0);
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          const R p = R(0.5) * (dF[c] + alpha * dq[c]);
-          const R n = R(0.5) * (dF[c] - alpha * dq[c]);
-          dfp[c * cells + si] = p;
-          dfm[c * cells + si] = n;
-          if constexpr (FP32) m = fmaxf(m, fmaxf(fabsf(p), fabsf(n)));
+          dfp[c * cells + si] = R(0.5) * (dF[c] + alpha * dq[c]);
+          dfm[c * cells + si] = R(0.5) * (dF[c] - alpha * dq[c]);
         }
-        if constexpr (FP32) mx[si] = m;
       }
     });
   }
@@ -694,11 +667,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
       for (int c = 0; c < NV; ++c) C[c] = R(0);
       unsigned fix = 0;
-      R mwin = R(0);  // largest |df| over the face's windows (FP32 near-tie test)
-      if constexpr (FP32) {
-#pragma unroll
-        for (int e = j - G + 1; e <= j + G - 1; ++e) mwin = fmaxf(mwin, mx[sidx(a, e)]);
-      }
 #pragma unroll 1
       for (int v = 0; v < NV; ++v) {
         R L[NV];
@@ -707,38 +675,24 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         } else {
           L[0] = R(1);
         }
-        // coarse rounding bound of every indicator of this field: Pascal sums
-        // of e_i <= sum|L| * mwin reach at most 2^(ORDER-1) times that
-        R coarse = R(0);
-        if constexpr (FP32) {
-          R ln = R(0);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) ln += fabsf(L[c]);
-          coarse = feps * R(1 << (ORDER - 1)) * ln * mwin;
-        }
         // f^+ then mirrored f^- window, one live at a time
         R cv = R(0);
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
-          R d[8];
-          window(a, j, sgn, L, d);
-          R IS[9], best;
-          int pick;
-          bool thr;
-          const R corr = eno_core<ORDER, R>(d, delta, IS, pick, thr, best);
+          R d[8], mag[8];
           if constexpr (FP32) {
-            // near-tie test: a coarse bound first (window maximum), the exact
-            // per-candidate bound only when the coarse one cannot rule it out
-            float tol[9];
+            window_mag(a, j, sgn, L, d, mag);
+          } else {
+            window(a, j, sgn, L, d);
 #pragma unroll
-            for (int c = 0; c < 9; ++c) tol[c] = coarse;
-            if (near_tie<ORDER>(IS, pick, thr, best, delta, tie_rel, tol)) {
-              R mag[8];
-              window_mag(a, j, sgn, L, d, mag);
-              pascal_tol<ORDER>(mag, feps, tol);
-              if (near_tie<ORDER>(IS, pick, thr, best, delta, tie_rel, tol))
-                fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 in phase 2b
-            }
+            for (int i = 0; i < 8; ++i) mag[i] = R(0);
+          }
+          int pick;
+          bool marg = false;
+          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
+                                              pick, marg);
+          if constexpr (FP32) {
+            if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 in phase 2b
           }
           if ((mode & kModeFlux) && A.idx_out && own) {
             const long long nf = A.ncell / g.nd * (g.nd + 1);
@@ -859,7 +813,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         R d[8];
         window(al, j, sgn, L, d);
         int pick_old;
-        const R corr_old = eno_select<ORDER, R>(d, delta, pick_old);
+        bool m;
+        const R nomx[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        const R corr_old = eno_select<ORDER, R, false>(d, delta, tie_rel, nomx, R(0), pick_old, m);
         if (pick != pick_old) {
           R corr = R(0);
 #pragma unroll
