@@ -39,6 +39,23 @@ BYTES_PER_CELL_Y = 32 + 16 + 32  # y sweep, stage 0: read U^n (FP64) and L_x (FP
 WORKLOAD = "euler2d-4096x4096-quadrant-riemann-ao5"
 
 
+def max_over_ranks(ms, device):
+    """Slowest rank's time (ms); the whole job takes as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, ms_max, world_size):
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time
+    (each rank advances its own replica of the workload: weak scaling)."""
+    return units_per_rank * world_size / (ms_max / 1e3)
+
+
 def _dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,12 +239,7 @@ def run_gpu(args):
         e1.record(stream)
         s.sync()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), "cuda")
 
     cells = N_CELLS * N_CELLS
     # ---- FP32-bulk (the line's value)
@@ -272,11 +284,11 @@ def run_gpu(args):
         s32.advance_steps(1, CFL)
         s32.get_state(host_out.numpy())
     torch.cuda.synchronize()
-    e2e_sec = time.perf_counter() - t0
-    e2e_value = cells * 3 * ke2e / e2e_sec * ws
+    e2e_sec = max_over_ranks(time.perf_counter() - t0, "cuda")
+    e2e_value = job_value(cells * 3 * ke2e, e2e_sec * 1e3, ws)
 
-    value = cells * 3 * args.steps / (ms32 / 1e3) * ws
-    value64 = cells * 3 * k64 / (ms64 / 1e3) * ws
+    value = job_value(cells * 3 * args.steps, ms32, ws)
+    value64 = job_value(cells * 3 * k64, ms64, ws)
 
     # Roofline of the dominant FP32-bulk kernel, the y-axis sweep (largest
     # share of a step in the launch list): it adds L_x, combines and, on the
