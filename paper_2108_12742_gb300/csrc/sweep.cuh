@@ -101,6 +101,42 @@ __device__ __forceinline__ float okey(float a) { return a; }
 template <typename R>
 __device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; }
 
+// Conversions between FP64 and FP32 on the integer units.  The hardware
+// conversion instructions issue to the FP64 unit, which the FP32 bulk path
+// otherwise leaves to the state update; these give the same bits for every
+// value of normal FP32 magnitude.
+// f32_rn: round to nearest even at mantissa bit 29 (the carry runs into the
+// exponent); magnitudes below the smallest normal float give a signed zero,
+// magnitudes from 2^128 up, infinities and NaN give NaN.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned lo = __double2loint(x), hi = __double2hiint(x);
+  const unsigned long long b =
+      ((static_cast<unsigned long long>(hi) << 32) | lo) + (0x0FFFFFFFull + ((lo >> 29) & 1u));
+  unsigned r = static_cast<unsigned>(b >> 29) - (896u << 23);  // exponent bias 1023 -> 127
+  r = (r & 0x7FFFFFFFu) | (hi & 0x80000000u);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e - 897u > 253u) r = e < 897u ? (hi & 0x80000000u) : 0x7FC00000u;
+  return __uint_as_float(r);
+}
+// f64_of: exact widening; zero and subnormal floats give a signed zero,
+// infinities and NaN give NaN.
+__device__ __forceinline__ double f64_of(float x) {
+  const unsigned u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
+  unsigned hi = (a >> 3) + (896u << 20), lo = u << 29;  // exponent bias 127 -> 1023
+  if (a < 0x00800000u) hi = lo = 0u;
+  if (a >= 0x7F800000u) hi = 0x7FF80000u, lo = 0u;
+  return __hiloint2double(static_cast<int>(hi | (u & 0x80000000u)), static_cast<int>(lo));
+}
+// FP64 value in the bulk precision, and a bulk value widened to FP64.
+template <typename R>
+__device__ __forceinline__ R to_bulk(double x);
+template <>
+__device__ __forceinline__ double to_bulk<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_bulk<float>(double x) { return f32_rn(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f64_of(x); }
+
 // ENO-AO choice on one window of first differences d[LO..HI] (d[i] between
 // offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
 // CHECK is set, 'marginal' reports a decision that rounding of size tol_abs
@@ -559,6 +595,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const R tie_rel = (R)A.tie_rel;
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
+  const R inv_dx_r = (R)inv_dx;
+  const float gamma_f = (float)A.gamma;
   // Shared-memory rows of SE cells per line for every axis: unit stride
   // along the swept axis (window offsets are immediates); SE is odd, so the
   // y/z sweeps, whose lanes run across lines, hit distinct banks.
@@ -614,7 +652,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       load_state<NV, COHERENT>(A.u_in, A.cstride, la + sa * g.stride_d, dir, qa64);
       R qa[NV];
 #pragma unroll
-      for (int c = 0; c < NV; ++c) qa[c] = (R)qa64[c];
+      for (int c = 0; c < NV; ++c) qa[c] = to_bulk<R>(qa64[c]);
       const int si = sidx(a, e);
       if constexpr (NP > 0) {
         if (e >= G - 1 && e <= G + nts) {
@@ -631,8 +669,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         R qb[NV], dq[NV], dF[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          qb[c] = (R)qb64[c];
-          dq[c] = (R)(qb64[c] - qa64[c]);
+          qb[c] = to_bulk<R>(qb64[c]);
+          dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
         }
         flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
 #pragma unroll
@@ -863,7 +901,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       for (int c = 0; c < NV; ++c) {
         const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
         const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
-        A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + (double)Cf[c * cells + sidx(a, j)];
+        A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + to_f64(Cf[c * cells + sidx(a, j)]);
       }
     });
   } else {
@@ -877,7 +915,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       for (int c = 0; c < NV; ++c) {
         const R s = dfp[c * cells + sidx(a, e - 1)] + dfm[c * cells + sidx(a, e)] +
                     (Cf[c * cells + sidx(a, e)] - Cf[c * cells + sidx(a, e - 1)]);
-        r[c] = -s * (R)inv_dx;
+        r[c] = -s * inv_dx_r;
       }
       if (!(mode & kModeCombine)) {
         R* rb = reinterpret_cast<R*>(A.rhs);
@@ -896,7 +934,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         // to FP64 for the Runge-Kutta combine
         R Lsum = r[c];
         if (mode & kModeRhsAdd) Lsum = reinterpret_cast<const R*>(A.rhs)[k] + r[c];
-        const double Lk = (double)Lsum;
+        const double Lk = to_f64(Lsum);
         const double ui = A.u_in[k];
         double un;
         if (A.stage == 0) {
@@ -915,25 +953,28 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         // and |u| + c are FP32, the energy difference E - ke stays FP64.
         if (A.stage == 2) {
           if constexpr (NV > 1) {
-            const float rho = (float)unew[0];
+            const float rho = f32_rn(unew[0]);
             float m2 = 0.0f;
 #pragma unroll
             for (int c = 1; c < NV - 1; ++c) {
-              const float m = (float)unew[c];
+              const float m = f32_rn(unew[c]);
               m2 += m * m;
             }
             const float ke = __fdividef(0.5f * m2, rho);
-            const float p = (float)((A.gamma - 1.0) * (unew[NV - 1] - (double)ke));
+            const float p = f32_rn((A.gamma - 1.0) * (unew[NV - 1] - f64_of(ke)));
             const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
             if (!ok) {
               atomicOr(&st->err, kErrNonPhys);
               atomicMin(&st->err_cell, cell);
             } else if (mode & kModeAlpha) {
               const float ir = __fdividef(1.0f, rho);
-              const float cs = sqrtf((float)A.gamma * p * ir);
+              const float cs = sqrtf(gamma_f * p * ir);
 #pragma unroll
-              for (int d = 0; d < NV - 2; ++d)
-                amax[d] = fmax(amax[d], (double)(fabsf((float)unew[1 + d]) * ir + cs));
+              for (int d = 0; d < NV - 2; ++d) {
+                // non-negative: the bit patterns order like the values
+                const double s = f64_of(fabsf(f32_rn(unew[1 + d])) * ir + cs);
+                if (okey(s) > okey(amax[d])) amax[d] = s;
+              }
             }
           } else if (!isfinite(unew[0])) {
             atomicOr(&st->err, kErrNonPhys);
