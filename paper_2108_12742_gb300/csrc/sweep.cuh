@@ -261,6 +261,21 @@ __device__ __forceinline__ int perm_comp(int c, int dir) {
   return 1 + (dir + c - 1) % ND;
 }
 
+// Conserved component k of a state held in permuted order, by selects (an
+// index computed from the runtime axis would put the array in local memory).
+template <int NV, typename T>
+__device__ __forceinline__ T comp_of(const T (&up)[NV], int k, int dir) {
+  if constexpr (NV < 3) {
+    return up[k];
+  } else {
+    if (k == 0 || k == NV - 1) return up[k];
+    T r = up[1];
+#pragma unroll
+    for (int c = 2; c < NV - 1; ++c) r = perm_comp<NV>(c, dir) == k ? up[c] : r;
+    return r;
+  }
+}
+
 // Flux difference F(qb) - F(qa) along the sweep axis, written in differences
 // so that rounding scales with |dq| (Euler: F = [m, m u + p, m_t u, (E+p) u]).
 template <int NV, typename T>
@@ -381,10 +396,14 @@ __device__ __forceinline__ void left_row(const Eigen<NV, T>& E, int v, T (&L)[NV
     for (int t = 0; t < NT; ++t) L[2 + t] = E.b1 * E.vt[t];
     L[NV - 1] = -E.b1;
   } else {
+    // shear field v: selects instead of indexing by v, so that L, E stay
+    // in registers when the caller loops over v without unrolling
+    T w = E.vt[0];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) L[i] = T(0);
-    L[0] = -E.vt[v - 2];
-    L[v] = T(1);
+    for (int t = 1; t < NT; ++t) w = v - 2 == t ? E.vt[t] : w;
+#pragma unroll
+    for (int i = 1; i < NV; ++i) L[i] = i == v ? T(1) : T(0);
+    L[0] = -w;
   }
 }
 
@@ -406,10 +425,12 @@ __device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[
     for (int t = 0; t < NT; ++t) Rc[2 + t] = E.vt[t];
     Rc[NV - 1] = T(0.5) * E.q2;
   } else {
+    T w = E.vt[0];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) Rc[i] = T(0);
-    Rc[v] = T(1);
-    Rc[NV - 1] = E.vt[v - 2];
+    for (int t = 1; t < NT; ++t) w = v - 2 == t ? E.vt[t] : w;
+#pragma unroll
+    for (int i = 0; i < NV - 1; ++i) Rc[i] = i == v ? T(1) : T(0);
+    Rc[NV - 1] = w;
   }
 }
 
@@ -926,7 +947,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
         return;
       }
-      double unew[NV];
+      double up[NV], unew[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
         const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
@@ -945,8 +966,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
         }
         A.u_out[k] = un;
-        unew[perm_comp<NV>(c, dir)] = un;  // back in conserved order
+        up[c] = un;
       }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) unew[k] = comp_of<NV>(up, k, dir);  // conserved order
       if constexpr (FP32) {
         // FP32 bulk: the state is checked, and the next step's alpha taken,
         // on each step's final state only; the kinetic energy, sound speed
