@@ -240,8 +240,26 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
         if (c == pick) tp = tol[c];
       m = (best - delta) <= rel + tp;
       const R relA = tie_rel * best + tp;
+      // Candidates 3 and 4 (and 6 and 7 of ENO-AO7) take the minimum over
+      // two differences of which they share the middle one, b: with
+      // IS_lo = min(a, b) and IS_hi = min(b, c), IS_lo wins exactly when
+      // a < b and a < c, so the margin of the pair is max(a - b, a - c), not
+      // IS_lo - IS_hi (which is zero whenever b is the smaller of both).
+      R gap[9];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) m |= (c != pick) && (IS[c] - best <= relA + tol[c]);
+      for (int c = 0; c < NC; ++c) gap[c] = IS[c] - best;
+      if (pick == 4) {
+        const R a = rabs(s4[1]), b = rabs(s4[2]), c = rabs(s4[3]);
+        gap[3] = fmaxf(a - b, a - c);
+      }
+      if constexpr (ORDER == 7) {
+        if (pick == 7) {
+          const R a = rabs(s6[0]), b = rabs(s6[1]), c = rabs(s6[2]);
+          gap[6] = fmaxf(a - b, a - c);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) m |= (c != pick) && (gap[c] <= relA + tol[c]);
     }
     marginal = m;
   }
