@@ -264,7 +264,7 @@ enoao_status enqueue_batch(enoao_ctx* c, int nsteps, double cfl) {
   BatchState* b = c->batch;
   const int f32 = c->cfg.precision == ENOAO_FP32_BULK;
   const size_t smem = sweep_smem_bytes(b->nv, c->cfg.order, f32, 1, b->ts,
-                                       sweep_row_pitch(c->cfg.order, f32, 0, 1, b->ts));
+                                       sweep_row_pitch(b->nv, c->cfg.order, f32, 0, 1, b->ts));
   cudaError_t e = launch_batch(b->nv, c->cfg.order, f32, make_args(c, nsteps, cfl), b->block, smem,
                                c->sms, c->s);
   if (e != cudaSuccess)

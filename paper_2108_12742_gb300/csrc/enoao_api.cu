@@ -230,7 +230,7 @@ enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
   if (d == 0 && ta != 1 && ta != 2 && ta != 4 && ta != 8)
     return fail(c, ENOAO_EINVAL, "axis 0 needs 1, 2, 4 or 8 lines per tile");
   size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), ta, ts,
-                                 sweep_row_pitch(c->cfg.order, fp32(c), d, ta, ts));
+                                 sweep_row_pitch(c->nv, c->cfg.order, fp32(c), d, ta, ts));
   if (smem > 200 * 1024)
     return fail(c, ENOAO_EINVAL, "tile %dx%d needs %zu bytes of shared memory", ta, ts, smem);
   return ENOAO_OK;
@@ -260,7 +260,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.stage = stage;
   a.ta = c->ta[d];
   a.ts = c->ts[d];
-  a.se = sweep_row_pitch(c->cfg.order, fp32(c), d, a.ta, a.ts);
+  a.se = sweep_row_pitch(c->nv, c->cfg.order, fp32(c), d, a.ta, a.ts);
   const long long nd = c->cfg.n[d];
   a.tiles_s = (nd + a.ts - 1) / a.ts;
   if (d == 0) {

@@ -95,14 +95,15 @@ cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int*
 // the Euler equations) and, in FP32 bulk mode, one word of near-tie flags.
 // Row pitch (cells) of a tile's shared-memory rows.  x sweeps read along a
 // row (any pitch); y/z sweeps put lines on lanes, so the pitch must spread a
-// warp's lanes over distinct banks: odd for 32- and 64-line tiles and for
-// 8-byte elements, 2 (mod 4) for 16-line FP32 tiles (a warp then spans two
-// cells of 16 lines).
-inline int sweep_row_pitch(int order, int fp32, int dir, int ta, int ts) {
+// warp's lanes over distinct banks: odd for 32- and 64-line tiles, for 8-byte
+// elements and for FP32 four-component cells (one 16-byte vector per cell:
+// each quarter-warp access then covers eight distinct 16-byte bank groups),
+// 2 (mod 4) for other 16-line FP32 tiles (a warp spans two cells of 16 lines).
+inline int sweep_row_pitch(int nv, int order, int fp32, int dir, int ta, int ts) {
   const int G = order / 2 + 2;
   int se = ts + 2 * G;
   if (dir == 0) return se;
-  if (fp32 && ta == 16) {
+  if (fp32 && ta == 16 && nv != 4) {
     while (se % 4 != 2) ++se;
   } else {
     if (se % 2 == 0) ++se;

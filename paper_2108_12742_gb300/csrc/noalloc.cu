@@ -159,7 +159,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   a.bc = cfg->bc[0];
   a.ta = 1;
   a.ts = f32 ? 127 : 63;
-  a.se = sweep_row_pitch(cfg->order, f32, 0, a.ta, a.ts);
+  a.se = sweep_row_pitch(nv, cfg->order, f32, 0, a.ta, a.ts);
   a.tiles_s = (n + a.ts - 1) / a.ts;
   a.tiles_a = a.tiles_b = 1;
   a.ntiles = a.tiles_s;

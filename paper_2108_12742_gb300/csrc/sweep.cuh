@@ -603,6 +603,32 @@ __device__ __forceinline__ void for_items(int lgTA, int cnt, bool sfast, F&& bod
   }
 }
 
+// Per-cell vectors in shared memory.  FP32 four-component states (2D Euler)
+// are stored as one float4 per cell, so a cell moves in one 128-bit access;
+// every other case keeps one plane per component.  Both layouts take NV
+// values of R per cell slot.
+template <int NV, typename R>
+struct CellVec {
+  static constexpr bool kAoS = sizeof(R) == 4 && NV == 4;
+  __device__ __forceinline__ static void load(const R* base, int cells, int i, R (&v)[NV]) {
+    if constexpr (kAoS) {
+      const float4 t = reinterpret_cast<const float4*>(base)[i];
+      v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) v[c] = base[c * cells + i];
+    }
+  }
+  __device__ __forceinline__ static void store(R* base, int cells, int i, const R (&v)[NV]) {
+    if constexpr (kAoS) {
+      reinterpret_cast<float4*>(base)[i] = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) base[c * cells + i] = v[c];
+    }
+  }
+};
+
 // One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
 // constant of the swept axis and the step size; amax accumulates |u_d| + c of
 // combined states (last stage), nfall counts FP64 re-decisions.
@@ -640,6 +666,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // along the swept axis (window offsets are immediates); SE is odd, so the
   // y/z sweeps, whose lanes run across lines, hit distinct banks.
   auto sidx = [&](int a, int e) { return a * SE + e; };
+  using CV = CellVec<NV, R>;
   const int lgTA = __ffs(TA) - 1;  // TA is a power of two (checked on the host)
   (void)TS;
   // Projected window of face j (extended cells) onto the field with left
@@ -652,9 +679,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
     for (int i = GE::LO; i <= GE::HI; ++i) {
       const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+      R x[NV];
+      CV::load(src, cells, e, x);
       R acc = R(0);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) acc += L[c] * src[c * cells + e];
+      for (int c = 0; c < NV; ++c) acc += L[c] * x[c];
       d[i] = sgn == 0 ? acc : -acc;
     }
   };
@@ -666,12 +695,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
     for (int i = GE::LO; i <= GE::HI; ++i) {
       const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+      R x[NV];
+      CV::load(src, cells, e, x);
       R acc = R(0), mag = R(0);
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
-        const R x = src[c * cells + e];
-        acc += L[c] * x;
-        mag += rabs(L[c]) * rabs(x);
+        acc += L[c] * x[c];
+        mag += rabs(L[c]) * rabs(x[c]);
       }
       d[i] = sgn == 0 ? acc : -acc;
       m[i] = mag;
@@ -697,8 +727,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         if (e >= G - 1 && e <= G + nts) {
           R pr[NV];
           roe_prims<NV, R>(qa, gm1, pr);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) prim[c * cells + si] = pr[c];
+          CV::store(prim, cells, si, pr);
         }
       }
       if (e + 1 < cnt) {
@@ -712,11 +741,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
         }
         flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
+        R fp[NV], fm[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          dfp[c * cells + si] = R(0.5) * (dF[c] + alpha * dq[c]);
-          dfm[c * cells + si] = R(0.5) * (dF[c] - alpha * dq[c]);
+          fp[c] = R(0.5) * (dF[c] + alpha * dq[c]);
+          fm[c] = R(0.5) * (dF[c] - alpha * dq[c]);
         }
+        CV::store(dfp, cells, si, fp);
+        CV::store(dfm, cells, si, fm);
       }
     });
   }
@@ -731,11 +763,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       Eigen<NV, R> E;
       if constexpr (NV > 1) {
         R pl[NV], prr[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          pl[c] = prim[c * cells + sidx(a, j)];
-          prr[c] = prim[c * cells + sidx(a, j + 1)];
-        }
+        CV::load(prim, cells, sidx(a, j), pl);
+        CV::load(prim, cells, sidx(a, j + 1), prr);
         roe_eigen<NV, R>(pl, prr, gm1, E);
       }
       const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
@@ -788,8 +817,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
       }
       const int sj = sidx(a, j);
-#pragma unroll
-      for (int c = 0; c < NV; ++c) Cf[c * cells + sj] = C[c];
+      CV::store(Cf, cells, sj, C);
       if constexpr (FP32) fixmask[sj] = fix;
     });
   }
@@ -864,11 +892,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       Eigen<NV, R> E;
       if constexpr (NV > 1) {
         R pl[NV], prr[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          pl[c] = prim[c * cells + sidx(al, j)];
-          prr[c] = prim[c * cells + sidx(al, j + 1)];
-        }
+        CV::load(prim, cells, sidx(al, j), pl);
+        CV::load(prim, cells, sidx(al, j + 1), prr);
         roe_eigen<NV, R>(pl, prr, gm1, E);
       }
       const long long gface = g.s0 + f;
@@ -914,8 +939,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
       }
       const int sj = sidx(al, j);
+      R Cv[NV];
+      CV::load(Cf, cells, sj, Cv);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) Cf[c * cells + sj] += dC[c];
+      for (int c = 0; c < NV; ++c) Cv[c] += dC[c];
+      CV::store(Cf, cells, sj, Cv);
     }
     __syncthreads();
   }
@@ -936,11 +964,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       phys_flux<NV>(ql, A.gamma - 1.0, A.adv_speed, Fl);
       phys_flux<NV>(qr, A.gamma - 1.0, A.adv_speed, Fr);
       const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+      R Cv[NV];
+      CV::load(Cf, cells, sidx(a, j), Cv);
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
         const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
         const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
-        A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + to_f64(Cf[c * cells + sidx(a, j)]);
+        A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + to_f64(Cv[c]);
       }
     });
   } else {
@@ -949,11 +979,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       if (g.a0 + a >= g.na) return;
       const int e = G + t;
       const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
-      R r[NV];
+      R r[NV], p0[NV], m1[NV], c1[NV], c0[NV];
+      CV::load(dfp, cells, sidx(a, e - 1), p0);
+      CV::load(dfm, cells, sidx(a, e), m1);
+      CV::load(Cf, cells, sidx(a, e), c1);
+      CV::load(Cf, cells, sidx(a, e - 1), c0);
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
-        const R s = dfp[c * cells + sidx(a, e - 1)] + dfm[c * cells + sidx(a, e)] +
-                    (Cf[c * cells + sidx(a, e)] - Cf[c * cells + sidx(a, e - 1)]);
+        const R s = p0[c] + m1[c] + (c1[c] - c0[c]);
         r[c] = -s * inv_dx_r;
       }
       if (!(mode & kModeCombine)) {
