@@ -216,7 +216,7 @@ void default_tiles(enoao_ctx* c) {
       c->ts[d] = 63;
     } else {
       c->ta[d] = f32 ? 16 : 32;
-      c->ts[d] = f32 ? 31 : 15;
+      c->ts[d] = f32 ? 23 : 15;  // FP32 2D Euler: six 36 KB blocks per SM
     }
     c->block[d] = 128;
   }
@@ -792,7 +792,7 @@ enoao_status enoao_autotune(enoao_ctx* c) {
           if (c->cfg.ndim > 1 || ta == 1) cands.push_back({ta, ts});
     } else {
       const int tas[] = {16, 32, 64};
-      const int tss[] = {7, 15, 31, 63};
+      const int tss[] = {7, 15, 23, 31, 63};
       for (int ta : tas)
         for (int ts : tss) cands.push_back({ta, ts});
     }

@@ -1083,13 +1083,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 }
 
 // Minimum resident blocks per SM asked of the compiler for the FP32-bulk
-// sweep (caps its registers at 65536 / (128 * min blocks)).
-#ifndef ENOAO_FP32_MIN_BLOCKS
-#define ENOAO_FP32_MIN_BLOCKS 4
+// sweep (caps its registers at 65536 / (128 * min blocks)): the sweep is
+// latency-bound, so six blocks (80 registers, a few spilled) beat four
+// without spills for ENO-AO5; ENO-AO7 keeps more live values and takes five.
+#ifndef ENOAO_FP32_MIN_BLOCKS_AO5
+#define ENOAO_FP32_MIN_BLOCKS_AO5 6
 #endif
+#ifndef ENOAO_FP32_MIN_BLOCKS_AO7
+#define ENOAO_FP32_MIN_BLOCKS_AO7 5
+#endif
+template <int ORDER, typename R>
+constexpr int sweep_min_blocks() {
+  return sizeof(R) == 8 ? 1 : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5 : ENOAO_FP32_MIN_BLOCKS_AO7);
+}
 
 template <int NV, int ORDER, typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? ENOAO_FP32_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
     sweep_kernel(const SweepArgs A) {
   constexpr bool FP32 = sizeof(R) == 4;
   StepState* st = A.st;
