@@ -165,8 +165,7 @@ namespace {
 
 template <int NV, int ORDER, typename R>
 cudaError_t launch_batch_t(const BatchArgs& b, int block, size_t smem, int sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel<NV, ORDER, R>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(batch_kernel<NV, ORDER, R>, smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<NV, ORDER, R>, block, smem);

@@ -90,6 +90,19 @@ cudaError_t sweep_configure_fp32(int nv, int order, size_t smem);
 cudaError_t sweep_occupancy_fp64(int nv, int order, int block, size_t smem, int* per_sm);
 cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm);
 
+// Raises a kernel's dynamic shared-memory limit to at least smem, never
+// lowers it: the limit belongs to the kernel, not to one launch, and the
+// axes and tiles of one kernel (and launches captured earlier into a graph)
+// need different sizes.
+template <typename Kernel>
+cudaError_t raise_smem_limit(Kernel* kernel, size_t smem) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 // Dynamic shared memory of one sweep block: per extended cell, the split
 // differences (2 nv), the face corrections (nv), the Roe ingredients (nv for
 // the Euler equations) and, in FP32 bulk mode, one word of near-tie flags.

@@ -13,8 +13,7 @@ static cudaError_t launch_one(const SweepArgs& a, int grid, int block, size_t sm
 
 template <int NV, int ORDER>
 static cudaError_t configure_one(size_t smem) {
-  return cudaFuncSetAttribute(sweep_kernel<NV, ORDER, float>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return raise_smem_limit(sweep_kernel<NV, ORDER, float>, smem);
 }
 
 template <int NV, int ORDER>
