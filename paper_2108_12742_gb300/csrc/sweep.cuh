@@ -425,6 +425,17 @@ __device__ __forceinline__ void left_row(const Eigen<NV, T>& E, int v, T (&L)[NV
   }
 }
 
+// Component v (a shear field, 2 <= v <= NV - 2) of a permuted vector, by
+// selects so that the vector stays in registers.
+template <int NV, typename T>
+__device__ __forceinline__ T shear_comp(const T (&x)[NV], int v) {
+  static_assert(NV >= 4, "shear fields exist for NV >= 4");
+  T r = x[2];
+#pragma unroll
+  for (int c = 3; c < NV - 1; ++c) r = v == c ? x[c] : r;
+  return r;
+}
+
 // Column v of R.
 template <int NV, typename T>
 __device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[NV]) {
@@ -707,6 +718,40 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       m[i] = mag;
     }
   };
+  // The same for shear field v, whose left row is e_v - w e_0 (w its
+  // tangential Roe velocity): one multiply-add per difference instead of NV.
+  auto window_shear = [&](int a, int j, int sgn, int v, R w, R (&d)[8], R (&m)[8]) {
+    if constexpr (NV >= 4) {
+      const R* src = sgn == 0 ? dfp : dfm;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) d[i] = m[i] = R(0);
+#pragma unroll
+      for (int i = GE::LO; i <= GE::HI; ++i) {
+        const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+        R x[NV];
+        CV::load(src, cells, e, x);
+        const R xv = shear_comp<NV>(x, v);
+        const R acc = xv - w * x[0];
+        d[i] = sgn == 0 ? acc : -acc;
+        if constexpr (FP32) m[i] = rabs(xv) + rabs(w) * rabs(x[0]);
+      }
+    }
+  };
+  // Projected window of field v (the same arithmetic in phase 2 and in the
+  // phase-2b check of a flagged choice, which must reproduce its pick).
+  auto field_window = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R (&d)[8],
+                          R (&mag)[8]) {
+    const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+    if (shear) {
+      window_shear(a, j, sgn, v, w, d, mag);
+    } else if constexpr (FP32) {
+      window_mag(a, j, sgn, L, d, mag);
+    } else {
+      window(a, j, sgn, L, d);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) mag[i] = R(0);
+    }
+  };
   const int nts = g.nts;
   const int sext = nts + 2 * G;  // extended cells in use
 
@@ -775,9 +820,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       unsigned fix = 0;
 #pragma unroll 1
       for (int v = 0; v < NV; ++v) {
-        R L[NV];
+        // shear fields (2D/3D Euler) have a sparse left row e_v - w e_0
+        const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+        R L[NV], w = R(0);
         if constexpr (NV > 1) {
           left_row<NV, R>(E, v, L);
+          if constexpr (NV >= 4) w = -L[0];
         } else {
           L[0] = R(1);
         }
@@ -786,13 +834,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
           R d[8], mag[8];
-          if constexpr (FP32) {
-            window_mag(a, j, sgn, L, d, mag);
-          } else {
-            window(a, j, sgn, L, d);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) mag[i] = R(0);
-          }
+          field_window(a, j, sgn, v, L, w, d, mag);
           int pick;
           bool marg = false;
           R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
@@ -806,6 +848,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
             A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
           }
           cv += corr;
+        }
+        if constexpr (NV >= 4) {
+          if (shear) {
+            // column v of R is e_v + w e_{NV-1}
+#pragma unroll
+            for (int c = 2; c < NV - 1; ++c) C[c] += c == v ? cv : R(0);
+            C[NV - 1] += w * cv;
+            continue;
+          }
         }
         if constexpr (NV > 1) {
           R Rc[NV];
@@ -906,14 +957,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         if (!(fix & (1u << k))) continue;
         const int v = k >> 1, sgn = k & 1;
         const int pick = (int)((picks >> (4 * k)) & 15ull);
-        R L[NV];
+        const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+        R L[NV], w = R(0);
         if constexpr (NV > 1) {
           left_row<NV, R>(E, v, L);
+          if constexpr (NV >= 4) w = -L[0];
         } else {
           L[0] = R(1);
         }
-        R d[8];
-        window(al, j, sgn, L, d);
+        R d[8], mag[8];
+        field_window(al, j, sgn, v, L, w, d, mag);
         int pick_old;
         bool m;
         const R nomx[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -923,7 +976,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
           for (int i = GE::LO; i <= GE::HI; ++i) corr += bcoef<R>(pick, i) * d[i];
           const R dv = corr - corr_old;
-          if constexpr (NV > 1) {
+          if (shear) {
+#pragma unroll
+            for (int c = 2; c < NV - 1; ++c) dC[c] += c == v ? dv : R(0);
+            dC[NV - 1] += w * dv;
+          } else if constexpr (NV > 1) {
             R Rc[NV];
             right_col<NV, R>(E, v, Rc);
 #pragma unroll
