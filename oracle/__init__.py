@@ -48,7 +48,7 @@ class Problem(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int), ("system", ctypes.c_int), ("order", ctypes.c_int),
         ("nthreads", ctypes.c_int), ("n", ctypes.c_long * 3),
-        ("dx", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("pad", ctypes.c_int),
+        ("dx", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("alpha_per_stage", ctypes.c_int),
         ("adv_speed", ctypes.c_double), ("gamma", ctypes.c_double),
         ("delta", ctypes.c_double),
     ]
@@ -87,8 +87,10 @@ def _dp(a):
 
 
 def make_problem(shape, lo, hi, system=EULER, order=5, bc=TRANSMISSIVE,
-                 adv_speed=1.0, gamma=1.4, delta=1e-5, nthreads=0) -> Problem:
-    """shape = (nx,) / (nx, ny) / (nx, ny, nz); lo/hi per axis; bc scalar or per axis."""
+                 adv_speed=1.0, gamma=1.4, delta=1e-5, nthreads=0,
+                 alpha_per_stage=False) -> Problem:
+    """shape = (nx,) / (nx, ny) / (nx, ny, nz); lo/hi per axis; bc scalar or per axis;
+    alpha_per_stage: each Runge-Kutta stage splits with the alpha of its own input state."""
     ndim = len(shape)
     P = Problem()
     P.ndim, P.system, P.order, P.nthreads = ndim, system, order, nthreads
@@ -101,6 +103,7 @@ def make_problem(shape, lo, hi, system=EULER, order=5, bc=TRANSMISSIVE,
         else:
             P.n[d], P.dx[d], P.bc[d] = 1, 1.0, PERIODIC
     P.adv_speed, P.gamma, P.delta = adv_speed, gamma, delta
+    P.alpha_per_stage = int(bool(alpha_per_stage))
     return P
 
 

@@ -489,32 +489,48 @@ int or_alpha(const or_problem *P, const double *U, double *alpha) {
   return 0;
 }
 
-int or_step(const or_problem *P, double *U, double dt) {
-  double alpha[3];
-  int st = or_alpha(P, U, alpha);
-  if (st) return st;
-  return or_step_alpha(P, U, dt, alpha);
-}
-
-int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha) {
+/* The three stages of the third-order TVD Runge-Kutta scheme (Sec. 2).
+ * Stage 0 splits with alpha0; with per_stage set, stages 1 and 2 split with
+ * the alpha of their own input state (u1, u2) instead. */
+static int rk3_step(const or_problem *P, double *U, double dt, const double *alpha0,
+                    int per_stage) {
   int nv = or_nvars(P);
   long M = (long)nv * n_cells(P);
   double *u0 = malloc(sizeof(double) * M);
   double *L = malloc(sizeof(double) * M);
+  double alpha[3] = {alpha0[0], alpha0[1], alpha0[2]};
+  int st = 0;
   memcpy(u0, U, sizeof(double) * M);
   /* u1 = u0 + dt L(u0) */
   or_rhs(P, U, alpha, L);
   for (long i = 0; i < M; ++i) U[i] = u0[i] + dt * L[i];
   /* u2 = 3/4 u0 + 1/4 (u1 + dt L(u1)) */
-  or_rhs(P, U, alpha, L);
-  for (long i = 0; i < M; ++i) U[i] = 0.75 * u0[i] + 0.25 * (U[i] + dt * L[i]);
-  /* u^{n+1} = 1/3 u0 + 2/3 (u2 + dt L(u2)) */
-  or_rhs(P, U, alpha, L);
-  for (long i = 0; i < M; ++i)
-    U[i] = (1.0 / 3.0) * u0[i] + (2.0 / 3.0) * (U[i] + dt * L[i]);
+  if (per_stage) st = or_alpha(P, U, alpha);
+  if (!st) {
+    or_rhs(P, U, alpha, L);
+    for (long i = 0; i < M; ++i) U[i] = 0.75 * u0[i] + 0.25 * (U[i] + dt * L[i]);
+    /* u^{n+1} = 1/3 u0 + 2/3 (u2 + dt L(u2)) */
+    if (per_stage) st = or_alpha(P, U, alpha);
+  }
+  if (!st) {
+    or_rhs(P, U, alpha, L);
+    for (long i = 0; i < M; ++i)
+      U[i] = (1.0 / 3.0) * u0[i] + (2.0 / 3.0) * (U[i] + dt * L[i]);
+  }
   free(u0);
   free(L);
-  return 0;
+  return st;
+}
+
+int or_step(const or_problem *P, double *U, double dt) {
+  double alpha[3];
+  int st = or_alpha(P, U, alpha);
+  if (st) return st;
+  return rk3_step(P, U, dt, alpha, P->alpha_per_stage && P->system == OR_EULER);
+}
+
+int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha) {
+  return rk3_step(P, U, dt, alpha, 0);
 }
 
 int or_advance(const or_problem *P, double *U, double t_end, double cfl,

@@ -31,7 +31,8 @@ typedef struct {
   long n[3];         /* cells per axis (unused axes: 1) */
   double dx[3];      /* grid spacing per axis */
   int bc[3];         /* OR_PERIODIC or OR_TRANSMISSIVE per axis */
-  int pad;
+  int alpha_per_stage; /* 0: alpha of U^n for all three stages; 1: each stage
+                          takes alpha of its own input state (dt from U^n) */
   double adv_speed;  /* a in f(u) = a*u (scalar only) */
   double gamma;      /* ratio of specific heats (Euler only) */
   double delta;      /* selection threshold of Sec. 3.2 (1e-5 in the paper) */
@@ -78,12 +79,14 @@ int or_rhs(const or_problem *P, const double *U, const double *alpha,
            double *rhs);
 
 /* One third-order TVD Runge-Kutta step of size dt, alpha taken from U at the
- * start of the step.  U is updated in place. */
+ * start of the step (and, with alpha_per_stage, from each later stage's
+ * input state for that stage).  U is updated in place. */
 int or_step(const or_problem *P, double *U, double dt);
 
-/* The same step with the splitting constants alpha given (alpha is a
- * property of the whole mesh, so a sub-block of a larger grid must be
- * stepped with the full grid's alpha). */
+/* The same step with the splitting constants alpha given for all three
+ * stages (alpha is a property of the whole mesh, so a sub-block of a larger
+ * grid must be stepped with the full grid's alpha); alpha_per_stage is not
+ * consulted. */
 int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha);
 
 /* Advance to t_end.  dt = cfl / sum_d(alpha_d/dx_d) when dt_fixed <= 0,

@@ -127,3 +127,70 @@ def test_3d_axis_cycle_symmetry(oracle_mod):
     a = oracle_mod.rhs(P, U)
     b = oracle_mod.rhs(P, cyc(U))
     assert np.allclose(cyc(a), b, rtol=0, atol=1e-12 * np.abs(a).max())
+
+
+# ------------------------------------------------------------- per-stage alpha
+# Sec. 2 fixes alpha as the largest |f'(u)| over the mesh without saying on
+# which state; the per-stage option evaluates it on each Runge-Kutta stage's
+# input state (dt still from U^n).
+
+def test_per_stage_alpha_is_inert_for_advection(oracle_mod):
+    # f = a u: |f'| = |a| on every state, so both options give the same bits
+    n = 64
+    U0 = inputs.advection_random(n, seed=12)
+    P1 = oracle_mod.make_problem((n,), (-1.0,), (1.0,), system=0, order=7, bc=0, adv_speed=0.9)
+    P2 = oracle_mod.make_problem((n,), (-1.0,), (1.0,), system=0, order=7, bc=0, adv_speed=0.9,
+                                 alpha_per_stage=True)
+    assert np.array_equal(oracle_mod.step(P1, U0, 0.01), oracle_mod.step(P2, U0, 0.01))
+
+
+def test_per_stage_alpha_where_the_fastest_cell_is_untouched(oracle_mod):
+    # The fastest cells (|u| + c largest) sit in a constant stretch that no wave
+    # reaches within one step, so every stage sees the same alpha: the two
+    # options agree bit for bit.  With the fastest cells inside the moving
+    # part, the stage alphas change and so does the result.
+    n = 200
+    x = (np.arange(n) + 0.5) / n
+    rho = np.where(x < 0.3, 1.0, 0.125)
+    p = np.where(x < 0.3, 1.0, 0.1)
+    u = np.where(x > 0.85, 1.5, 0.0)   # fast, uniform right end, far from the jump at 0.3
+    U = np.stack([rho, rho * u, p / 0.4 + 0.5 * rho * u * u]).reshape(3, 1, 1, n)
+    P1 = oracle_mod.make_problem((n,), (0.0,), (1.0,), order=5)
+    P2 = oracle_mod.make_problem((n,), (0.0,), (1.0,), order=5, alpha_per_stage=True)
+    a = oracle_mod.alpha(P1, U)
+    # the max is attained in x > 0.85, where no wave arrives in one small step;
+    # the velocity jump at 0.85 itself moves, so keep dt small against it
+    dt = 0.1 / n / a[0]
+    fast = x > 0.9
+    assert np.abs(U[1, 0, 0] / U[0, 0, 0])[fast].max() + np.sqrt(1.4 * 0.1 / 0.125) == pytest.approx(a[0])
+    r1, r2 = oracle_mod.step(P1, U, dt), oracle_mod.step(P2, U, dt)
+    assert np.array_equal(r1[:, :, :, fast], r2[:, :, :, fast])
+    # the whole step agrees only if the stage alphas did not move; they do not
+    # here because the fastest cells stay bitwise constant
+    assert np.array_equal(r1, r2)
+
+    # now put the fastest gas in the compressing region: stage alphas differ
+    u2 = np.where((x > 0.25) & (x < 0.35), 2.0, 0.0)
+    U2 = np.stack([rho, rho * u2, p / 0.4 + 0.5 * rho * u2 * u2]).reshape(3, 1, 1, n)
+    dt2 = 0.5 / n / oracle_mod.alpha(P1, U2)[0]
+    s1, s2 = oracle_mod.step(P1, U2, dt2), oracle_mod.step(P2, U2, dt2)
+    d = np.abs(s1 - s2).max() / np.abs(s1).max()
+    assert 0.0 < d < 1e-2
+
+
+@pytest.mark.parametrize("order", [5, 7])
+def test_per_stage_alpha_conserves_and_keeps_constants(oracle_mod, order):
+    n = 24
+    U0 = inputs.euler2d_random(n, n, seed=8)
+    P = oracle_mod.make_problem((n, n), (0.0, 0.0), (1.0, 1.0), order=order,
+                                bc=oracle_mod.PERIODIC, alpha_per_stage=True)
+    U, _, k = oracle_mod.advance(P, U0, 10.0, cfl=0.4, max_steps=2)
+    assert k == 2
+    eps = np.finfo(float).eps
+    for v in range(4):
+        assert abs(U[v].sum() - U0[v].sum()) <= 10 * U0[v].size * eps * np.abs(U0[v]).max() * 2
+    C = _const_state(1, (16, 13), seed=3)
+    Pc = oracle_mod.make_problem((16, 13), (0.0, 0.0), (1.0, 1.0), order=order, bc=1,
+                                 alpha_per_stage=True)
+    Uc, _, _ = oracle_mod.advance(Pc, C, 1.0, cfl=0.5, max_steps=2)
+    assert np.abs(Uc - C).max() <= 8 * np.spacing(np.abs(C).max())
