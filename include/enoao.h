@@ -58,6 +58,11 @@ typedef enum {
 enum { ENOAO_SCALAR_ADVECTION = 0, ENOAO_EULER = 1 };
 enum { ENOAO_PERIODIC = 0, ENOAO_TRANSMISSIVE = 1 };
 enum { ENOAO_FP64 = 0, ENOAO_FP32_BULK = 1 };
+/* When alpha of the Lax-Friedrichs splitting (Sec. 2: the maximum of |f'(u)|
+ * over the mesh) is taken for the Euler equations: once per step from U^n
+ * for all three Runge-Kutta stages (the default), or per stage from that
+ * stage's input state.  dt always follows the CFL rule with alpha of U^n. */
+enum { ENOAO_ALPHA_PER_STEP = 0, ENOAO_ALPHA_PER_STAGE = 1 };
 
 typedef struct {
   int ndim;        /* 1, 2 or 3 */
@@ -70,7 +75,7 @@ typedef struct {
   double lo[3];    /* domain [lo, hi] per axis; dx = (hi - lo) / n */
   double hi[3];
   int bc[3];       /* ENOAO_PERIODIC or ENOAO_TRANSMISSIVE (zero-gradient) per axis */
-  int reserved;
+  int alpha_mode;  /* ENOAO_ALPHA_PER_STEP or ENOAO_ALPHA_PER_STAGE */
   double adv_speed;  /* scalar advection speed a */
   double gamma;      /* ratio of specific heats (Euler) */
   double delta;      /* selection threshold, 1e-5 in the paper (Sec. 3.2 remark) */
@@ -125,6 +130,14 @@ enoao_status enoao_init_state(enoao_ctx *ctx, const double *U, int on_device);
 
 /* Copies the current state U^n out (same layout). */
 enoao_status enoao_get_state(enoao_ctx *ctx, double *U, int on_device);
+
+/* Copies a Runge-Kutta stage state out (same layout): k = 0 is U^n (as
+ * enoao_get_state), k = 1 and 2 are U^(1) = U^n + dt L(U^n) and U^(2) of
+ * Sec. 2's third-order TVD scheme as the stages last wrote them -- after
+ * enoao_rk_stage(ctx, 0 or 1, dt) the state the next stage starts from, after
+ * a whole step the last step's.  For checking a step stage by stage.
+ * ENOAO_EINVAL for k outside 0..2 and for batched contexts. */
+enoao_status enoao_get_stage_state(enoao_ctx *ctx, int k, double *U, int on_device);
 
 /* Interface fluxes F_{j+1/2} of Eq. (1DWENOFD) along axis dir for the current
  * state, with alpha of the current state (Sec. 2, 3, 4).  Fhat has the state's

@@ -25,6 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "enoao.h")
 SCALAR_ADVECTION, EULER = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 FP64, FP32_BULK = 0, 1
+ALPHA_PER_STEP, ALPHA_PER_STAGE = 0, 1
 
 STATUS = {0: "ENOAO_OK", 1: "ENOAO_EINVAL", 2: "ENOAO_ENOMEM", 3: "ENOAO_ECUDA",
           4: "ENOAO_ENONPHYS", 5: "ENOAO_ETIMEOUT"}
@@ -40,7 +41,7 @@ class Config(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int), ("system", ctypes.c_int), ("order", ctypes.c_int),
         ("precision", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("lo", ctypes.c_double * 3),
-        ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("reserved", ctypes.c_int),
+        ("hi", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("alpha_mode", ctypes.c_int),
         ("adv_speed", ctypes.c_double), ("gamma", ctypes.c_double),
         ("delta", ctypes.c_double), ("tie_rel", ctypes.c_double),
     ]
@@ -84,6 +85,7 @@ def load():
         "enoao_last_error": (ctypes.c_char_p, [P]),
         "enoao_init_state": (ctypes.c_int, [P, P, ctypes.c_int]),
         "enoao_get_state": (ctypes.c_int, [P, P, ctypes.c_int]),
+        "enoao_get_stage_state": (ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int]),
         "enoao_reconstruct_fluxes": (ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int]),
         "enoao_rk_stage": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_double]),
         "enoao_advance": (ctypes.c_int, [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -131,7 +133,8 @@ def _stream_handle(stream):
 
 
 def make_config(shape, lo, hi, system=EULER, order=5, precision=FP64, bc=TRANSMISSIVE,
-                adv_speed=1.0, gamma=1.4, delta=1e-5, tie_rel=1e-3) -> Config:
+                adv_speed=1.0, gamma=1.4, delta=1e-5, tie_rel=1e-3,
+                alpha_mode=0) -> Config:
     lib = load()
     cfg = Config()
     lib.enoao_config_default(ctypes.byref(cfg))
@@ -142,6 +145,7 @@ def make_config(shape, lo, hi, system=EULER, order=5, precision=FP64, bc=TRANSMI
         if d < ndim:
             cfg.n[d], cfg.lo[d], cfg.hi[d], cfg.bc[d] = int(shape[d]), lo[d], hi[d], int(bcs[d])
     cfg.adv_speed, cfg.gamma, cfg.delta, cfg.tie_rel = adv_speed, gamma, delta, tie_rel
+    cfg.alpha_mode = alpha_mode
     return cfg
 
 
@@ -211,6 +215,14 @@ class Solver:
             out = np.empty(self.state_shape)
         p, dev = _ptr(out)
         self._check(self._lib.enoao_get_state(self._h, p, dev))
+        return out
+
+    def get_stage_state(self, k, out=None):
+        """Runge-Kutta stage state k (0: U^n, 1: U^(1), 2: U^(2)) as last written."""
+        if out is None:
+            out = np.empty(self.state_shape)
+        p, dev = _ptr(out)
+        self._check(self._lib.enoao_get_stage_state(self._h, k, p, dev))
         return out
 
     def face_shape(self, d):

@@ -38,6 +38,7 @@ struct BatchArgs {
   StepState* st;           // error word and FP64 re-decision count
   int ts;                  // cells per tile
   int bc;
+  int per_stage_alpha;     // 1: each stage splits with the alpha of its input state
   double gamma, adv_speed, delta, tie_rel;
 };
 
@@ -114,20 +115,27 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
       alpha = fabs(B.adv_speed);
     }
     double t = B.t[p], dt = 0.0;
+    const bool per_stage = NV > 1 && B.per_stage_alpha;
     for (int step = 0; step < B.nsteps; ++step) {
       dt = B.cfl / (alpha / dx);
-      double amax[3] = {0.0, 0.0, 0.0};
+      double a_stage = alpha;  // splitting constant of the current stage
       for (int stage = 0; stage < 3; ++stage) {
+        double amax[3] = {0.0, 0.0, 0.0};
         A.u_in = B.U[stage] + off;
         A.u0 = B.U[0] + off;
         A.u_out = B.U[stage == 2 ? 0 : stage + 1] + off;
         A.stage = stage;
-        A.mode = kModeCombine | (stage == 2 ? kModeAlpha : 0);
+        A.mode = kModeCombine | (stage == 2 || per_stage ? kModeAlpha : 0);
         for (long long tile = 0; tile < A.ntiles; ++tile)
-          sweep_tile<NV, ORDER, R, true>(A, tile_geo(A, tile), smem_raw, alpha, dt, amax, nfall);
+          sweep_tile<NV, ORDER, R, true>(A, tile_geo(A, tile), smem_raw, a_stage, dt, amax, nfall);
+        if constexpr (NV > 1) {
+          if (stage == 2)
+            alpha = block_max(amax[0], s_red);
+          else if (per_stage)
+            a_stage = block_max(amax[0], s_red);
+        }
       }
       t += dt;
-      if constexpr (NV > 1) alpha = block_max(amax[0], s_red);
     }
     if (threadIdx.x == 0) {
       B.t[p] = t;
@@ -256,6 +264,7 @@ BatchArgs make_args(enoao_ctx* c, int nsteps, double cfl) {
   a.adv_speed = c->cfg.adv_speed;
   a.delta = c->cfg.delta;
   a.tie_rel = c->cfg.tie_rel;
+  a.per_stage_alpha = c->cfg.alpha_mode == ENOAO_ALPHA_PER_STAGE;
   return a;
 }
 

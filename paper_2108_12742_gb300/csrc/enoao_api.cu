@@ -130,7 +130,7 @@ __global__ void step_begin_kernel(StepState* st, StepConsts k) {
     s += a / k.dx[d];
   }
   st->par = cur ^ 1;
-  for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = 0ull;
+  for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = st->alpha_stage[d] = 0ull;
   double dt = st->dt_fixed > 0.0 ? st->dt_fixed : st->cfl / s;
   st->last = 0;
   if (st->t + dt >= st->t_end) {
@@ -143,6 +143,16 @@ __global__ void step_begin_kernel(StepState* st, StepConsts k) {
 
 __global__ void finalize_kernel(StepState* st) { finalize_pending(st); }
 
+// Per-stage alpha: the next stage splits with the alpha of the state the
+// previous stage wrote (accumulated by that stage's last sweep).
+__global__ void stage_alpha_kernel(StepState* st, StepConsts k) {
+  if (st->skip) return;
+  for (int d = 0; d < k.ndim; ++d) {
+    st->alpha[d] = __longlong_as_double((long long)st->alpha_stage[d]);
+    st->alpha_stage[d] = 0ull;
+  }
+}
+
 // Manual stages (enoao_rk_stage): stage 0 begins a step with the caller's dt.
 __global__ void manual_stage_kernel(StepState* st, StepConsts k, int stage, double dt) {
   if (stage == 0) {
@@ -154,7 +164,7 @@ __global__ void manual_stage_kernel(StepState* st, StepConsts k, int stage, doub
                          ? __longlong_as_double((long long)st->alpha_acc[cur][d])
                          : fabs(k.adv_speed);
     st->par = cur ^ 1;
-    for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = 0ull;
+    for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = st->alpha_stage[d] = 0ull;
     st->last = 0;
     st->pending = 0;
   }
@@ -300,16 +310,27 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
 }
 
 // One Runge-Kutta stage: every axis, the last one combining.
+bool per_stage_alpha(const enoao_ctx* c) {
+  return c->cfg.system == ENOAO_EULER && c->cfg.alpha_mode == ENOAO_ALPHA_PER_STAGE;
+}
+
 enoao_status enqueue_stage(enoao_ctx* c, int stage) {
   const double* in = c->U[stage];                 // U^n, U1, U2
   double* out = c->U[stage == 2 ? 0 : stage + 1];  // U1, U2, U^{n+1}
   const int nd = c->cfg.ndim;
+  if (stage > 0 && per_stage_alpha(c)) {
+    stage_alpha_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
+    CU(c, cudaGetLastError());
+  }
+  // alpha of the written state: for the next step (stage 2), or for the next
+  // stage when each stage takes its own
+  const bool want_alpha = stage == 2 || per_stage_alpha(c);
   for (int d = 0; d < nd; ++d) {
     int mode;
     if (d < nd - 1)
       mode = kModeRhsStore | (d > 0 ? kModeRhsAdd : 0);
     else
-      mode = kModeCombine | (nd > 1 ? kModeRhsAdd : 0) | (stage == 2 ? kModeAlpha : 0);
+      mode = kModeCombine | (nd > 1 ? kModeRhsAdd : 0) | (want_alpha ? kModeAlpha : 0);
     enoao_status r = launch_sweep(c, d, stage, mode, in, out, nullptr, nullptr);
     if (r != ENOAO_OK) return r;
   }
@@ -443,6 +464,8 @@ static enoao_status validate(const enoao_config* cfg, bool batched) {
     return fail(nullptr, ENOAO_EINVAL, "gamma must exceed 1");
   if (!(cfg->delta >= 0.0)) return fail(nullptr, ENOAO_EINVAL, "delta must be >= 0");
   if (!(cfg->tie_rel >= 0.0)) return fail(nullptr, ENOAO_EINVAL, "tie_rel must be >= 0");
+  if (cfg->alpha_mode != ENOAO_ALPHA_PER_STEP && cfg->alpha_mode != ENOAO_ALPHA_PER_STAGE)
+    return fail(nullptr, ENOAO_EINVAL, "alpha_mode must be ENOAO_ALPHA_PER_STEP or _PER_STAGE");
   return ENOAO_OK;
 }
 
@@ -568,6 +591,20 @@ enoao_status enoao_get_state(enoao_ctx* c, double* U, int on_device) {
   enoao_status r = enter(c);
   if (r != ENOAO_OK) return r;
   CU(c, cudaMemcpyAsync(U, c->U[0], (size_t)c->nv * c->ncell * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+enoao_status enoao_get_stage_state(enoao_ctx* c, int k, double* U, int on_device) {
+  if (!c || !U) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  if (k < 0 || k > 2) return fail(c, ENOAO_EINVAL, "stage state k must be 0, 1 or 2");
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaMemcpyAsync(U, c->U[k], (size_t)c->nv * c->ncell * sizeof(double),
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
   r = leave(c);
   if (r != ENOAO_OK) return r;
@@ -722,7 +759,7 @@ enoao_status enoao_get_stats(enoao_ctx* c, enoao_stats* out) {
 int enoao_launches_per_step(const enoao_ctx* c) {
   if (!c) return 0;
   if (c->batch) return 0;  // one persistent launch covers every step
-  return 1 + 3 * c->cfg.ndim;
+  return 1 + 3 * c->cfg.ndim + (per_stage_alpha(c) ? 2 : 0);
 }
 
 enoao_status enoao_set_tiles(enoao_ctx* c, int dir, int ta, int ts) {

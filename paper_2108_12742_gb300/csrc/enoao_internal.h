@@ -33,6 +33,8 @@ struct StepState {
   unsigned long long tile_next;  // dynamic tile queue of the running sweep launch
   unsigned int blocks_done;      // blocks of the running sweep launch that have left it
   unsigned int pad2;
+  unsigned long long alpha_stage[3];  // per-stage alpha: running max over the
+                                      // state stage 0 or 1 writes (bit patterns)
 };
 
 constexpr int kErrNonPhys = 1;
@@ -42,7 +44,8 @@ constexpr int kErrTimeout = 2;
 constexpr int kModeRhsStore = 1;   // write this axis' L(u) into rhs
 constexpr int kModeRhsAdd = 2;     // add the stored rhs of earlier axes
 constexpr int kModeCombine = 4;    // Runge-Kutta combine into u_out
-constexpr int kModeAlpha = 8;      // accumulate alpha of u_out for the next step
+constexpr int kModeAlpha = 8;      // accumulate alpha of u_out: for the next step
+                                   // (stage 2) or the next stage (stages 0, 1)
 constexpr int kModeFlux = 16;      // write interface fluxes (and choices)
 
 struct SweepArgs {

@@ -79,6 +79,7 @@ __global__ void noalloc_alpha_kernel(const double* __restrict__ U, long long n, 
 
 __global__ void noalloc_alpha_set_kernel(StepState* st) {
   st->alpha[0] = __longlong_as_double((long long)st->alpha_acc[0][0]);
+  st->alpha_acc[0][0] = 0ull;  // ready for a per-stage alpha
 }
 
 // Device address of the fixed array on the current device, set up once per
@@ -112,6 +113,8 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   if (cfg->order != 5 && cfg->order != 7) return nofail(ENOAO_EINVAL, "order must be 5 or 7");
   if (cfg->precision != ENOAO_FP64 && cfg->precision != ENOAO_FP32_BULK)
     return nofail(ENOAO_EINVAL, "unknown precision");
+  if (cfg->alpha_mode != ENOAO_ALPHA_PER_STEP && cfg->alpha_mode != ENOAO_ALPHA_PER_STAGE)
+    return nofail(ENOAO_EINVAL, "unknown alpha_mode");
   if (cfg->bc[0] != ENOAO_PERIODIC && cfg->bc[0] != ENOAO_TRANSMISSIVE)
     return nofail(ENOAO_EINVAL, "unknown boundary condition");
   const long long n = cfg->n[0];
@@ -181,7 +184,13 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   // stage 2: U_out = 1/3 U^n + 2/3 (U2 + dt L(U2))
   const double* ins[3] = {U_in, U1, U2};
   double* outs[3] = {U1, U2, U_out};
+  const bool per_stage = nv > 1 && cfg->alpha_mode == ENOAO_ALPHA_PER_STAGE;
   for (int stage = 0; stage < 3; ++stage) {
+    if (stage > 0 && per_stage) {
+      // this stage splits with the alpha of its own input state
+      noalloc_alpha_kernel<<<ablocks, 256, 0, s>>>(ins[stage], n, nv, cfg->gamma, cfg->adv_speed, st);
+      noalloc_alpha_set_kernel<<<1, 1, 0, s>>>(st);
+    }
     a.u_in = ins[stage];
     a.u0 = U_in;
     a.u_out = outs[stage];

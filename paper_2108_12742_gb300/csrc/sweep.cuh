@@ -1080,8 +1080,29 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       for (int k = 0; k < NV; ++k) unew[k] = comp_of<NV>(up, k, dir);  // conserved order
       if constexpr (FP32) {
         // FP32 bulk: the state is checked, and the next step's alpha taken,
-        // on each step's final state only; the kinetic energy, sound speed
-        // and |u| + c are FP32, the energy difference E - ke stays FP64.
+        // on each step's final state; the kinetic energy, sound speed and
+        // |u| + c are FP32, the energy difference E - ke stays FP64.  The
+        // alpha of a later stage of the same step (per-stage alpha) is taken
+        // in FP64 like the FP64 path's: the stage's stencil choices must not
+        // depend on FP32 rounding of the splitting constant.
+        if constexpr (NV > 1) {
+          if (A.stage < 2 && (mode & kModeAlpha)) {
+            const double rho = unew[0];
+            double m2 = 0.0;
+#pragma unroll
+            for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
+            const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 / rho);
+            if (!(rho > 0.0 && p > 0.0 && isfinite(p))) {
+              atomicOr(&st->err, kErrNonPhys);
+              atomicMin(&st->err_cell, cell);
+            } else {
+              const double cs = sqrt(A.gamma * p / rho);
+#pragma unroll
+              for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
+            }
+            return;
+          }
+        }
         if (A.stage == 2) {
           if constexpr (NV > 1) {
             const float rho = f32_rn(unew[0]);
@@ -1123,7 +1144,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         if (!ok) {
           atomicOr(&st->err, kErrNonPhys);
           atomicMin(&st->err_cell, cell);
-        } else if ((mode & kModeAlpha) && A.stage == 2) {
+        } else if (mode & kModeAlpha) {
           const double cs = sqrt(A.gamma * p / rho);
 #pragma unroll
           for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
@@ -1189,7 +1210,7 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
   if constexpr (FP32) {
     if (nfall) atomicAdd(&st->fallbacks, nfall);
   }
-  if (NV > 1 && (mode & kModeAlpha) && A.stage == 2) {
+  if (NV > 1 && (mode & kModeAlpha)) {
     // block max of |u_d| + c, then one atomic per block and axis
     __shared__ double red[3][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1208,8 +1229,9 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
         double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        unsigned long long* acc = A.stage == 2 ? st->alpha_acc[st->par] : st->alpha_stage;
         if (threadIdx.x == 0 && d < A.ndim && v > 0.0)
-          atomicMax(&st->alpha_acc[st->par][d], (unsigned long long)__double_as_longlong(v));
+          atomicMax(&acc[d], (unsigned long long)__double_as_longlong(v));
       }
     }
   }

@@ -100,3 +100,30 @@ def test_batch_rejects_bad_input():
         with pytest.raises(eno.EnoaoError) as e:
             b.init_state(U)
         assert e.value.status == 4 and "cell 70" in str(e.value)
+
+
+@pytest.mark.parametrize("precision", [eno.FP64, eno.FP32_BULK])
+def test_batch_per_stage_alpha_matches_oracle(precision):
+    sizes = np.array([300, 97, 1200])
+    U = _batch(sizes, seed=11)
+    with eno.Batch(sizes, 0.0, 1.0, system=eno.EULER, order=5, precision=precision,
+                   alpha_mode=eno.ALPHA_PER_STAGE) as b:
+        b.init_state(U)
+        b.advance_steps(1, 0.5)
+        got = b.get_state()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i, n in enumerate(sizes):
+        Ui = U[:, off[i]:off[i + 1]].reshape(3, 1, 1, -1)
+        P = oracle.make_problem((int(n),), (0.0,), (1.0,), system=oracle.EULER, order=5,
+                                alpha_per_stage=True)
+        a = oracle.alpha(P, Ui)
+        dt = 0.5 / (a[0] / (1.0 / n))
+        ref = oracle.step(P, Ui, dt).reshape(3, -1)
+        g = got[:, off[i]:off[i + 1]]
+        if precision == eno.FP64:
+            assert np.abs(g - ref).max() / np.abs(ref).max() <= 1e-12, i
+        else:
+            # L1 always; max-norm outside near-tie flips of the later stages
+            assert np.abs(g - ref).mean() / np.abs(ref).mean() <= 1e-8, i
+            over = (np.abs(g - ref) > 1e-7 * np.abs(ref).max(axis=1, keepdims=True)).any(axis=0)
+            assert over.mean() <= 1e-3, i

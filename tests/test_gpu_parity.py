@@ -233,10 +233,13 @@ def test_errors_come_back_as_status_codes():
 # ---------------------------------------------------------------- FP32 bulk
 # The FP32-bulk path computes the reconstruction in FP32 from FP64 state
 # differences; its stated tolerances (relative to the field's max-norm) are
-# 1e-6 on interface fluxes and 1e-7 per step on the state, with at least
+# 1e-6 on interface fluxes and 1e-7 per step on the state, 1e-8 on the
+# state's L1 norm (mean |error| over mean |value|) per step, with at least
 # 99.9% of stencil choices equal to the FP64 oracle's.
 TOL32_FLUX = 1e-6
 TOL32_STEP = 1e-7
+TOL32_L1 = 1e-8
+
 
 
 @pytest.mark.parametrize("name", ["adv1d-square-ao7", "euler1d-riemann-ao5", "euler1d-riemann-ao7",
@@ -257,6 +260,7 @@ def test_fp32_bulk_against_oracle(name):
         got = s.get_state()
         ref = oracle.step(P, U0, s.stats().dt)
         assert relerr(got, ref) <= TOL32_STEP, relerr(got, ref)
+        assert np.abs(got - ref).mean() / np.abs(ref).mean() <= TOL32_L1
 
 
 # ------------------------------------------------- full size, bench launch config
@@ -329,3 +333,70 @@ def test_1d_results_do_not_depend_on_tiles_fp32():
             outs.append(s.get_state())
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
+
+
+# ------------------------------------------------------------- per-stage alpha
+@pytest.mark.parametrize("name", ["euler1d-riemann-ao5", "euler2d-random-ao7", "euler3d-blast-ao7"])
+def test_per_stage_alpha_step_matches_oracle(name):
+    # FP64, whole steps from identical inputs; cases whose fastest cells move,
+    # so that the stage alphas differ (on the four-quadrant data they sit in
+    # untouched quadrant interiors at first)
+    shape, lo, hi, system, order, bc, init, a = CASES[name]
+    P = oracle.make_problem(shape, lo, hi, system=system, order=order, bc=bc,
+                            alpha_per_stage=True)
+    Pstep = oracle.make_problem(shape, lo, hi, system=system, order=order, bc=bc)
+    U = np.ascontiguousarray(init())
+    with eno.Solver(shape, lo, hi, system=system, order=order, bc=bc,
+                    alpha_mode=eno.ALPHA_PER_STAGE) as s:
+        assert s.launches_per_step() == 1 + 3 * len(shape) + 2
+        for k in range(2):
+            s.init_state(U)
+            s.advance(1e9, cfl=0.5, max_steps=1)
+            st = s.stats()
+            got = s.get_state()
+            ref = oracle.step(P, U, st.dt)
+            assert relerr(got, ref) <= TOL64, (k, relerr(got, ref))
+            # the option is live on this data: the per-step result differs
+            assert relerr(oracle.step(Pstep, U, st.dt), ref) > 10 * TOL64
+            U = got
+
+
+@pytest.mark.parametrize("alpha_mode", [eno.ALPHA_PER_STEP, eno.ALPHA_PER_STAGE])
+@pytest.mark.parametrize("precision", [eno.FP64, eno.FP32_BULK])
+@pytest.mark.parametrize("name", ["euler1d-riemann-ao5", "euler2d-random-ao7", "euler3d-blast-ao7"])
+def test_stages_match_oracle_on_their_own_inputs(name, precision, alpha_mode):
+    # Each Runge-Kutta stage against the oracle's spatial operator applied to
+    # the stage state this path produced.  A whole FP32-bulk step is not a fair
+    # test: stages 2 and 3 start from states that differ from the oracle's by
+    # FP32 rounding, and a choice that is a near-tie at that level may go
+    # either way (on the 3D blast data with per-stage alpha one f^- choice
+    # flips between candidates 2 and 8, whose indicators are 7e-9 apart).
+    shape, lo, hi, system, order, bc, init, a = CASES[name]
+    P = oracle.make_problem(shape, lo, hi, system=system, order=order, bc=bc)
+    U = np.ascontiguousarray(init())
+    a0 = np.asarray(oracle.alpha(P, U))
+    dt = 0.5 / sum(a0[d] * shape[d] / (hi[d] - lo[d]) for d in range(len(shape)))
+    per_stage = alpha_mode == eno.ALPHA_PER_STAGE
+    with eno.Solver(shape, lo, hi, system=system, order=order, bc=bc, precision=precision,
+                    alpha_mode=alpha_mode) as s:
+        s.init_state(U)
+        G = [U]
+        for k in range(3):
+            s.rk_stage(k, dt)
+            G.append(s.get_stage_state(k + 1) if k < 2 else s.get_state())
+            a_used = np.asarray(oracle.alpha(P, G[k])) if per_stage else a0
+            nd = len(shape)
+            assert np.allclose(s.stats().alpha[:nd], a_used[:nd], rtol=1e-12, atol=0), k
+            Lk = oracle.rhs(P, G[k], a_used)
+            if k == 0:
+                ref = U + dt * Lk
+            elif k == 1:
+                ref = 0.75 * U + 0.25 * (G[1] + dt * Lk)
+            else:
+                ref = U / 3.0 + 2.0 / 3.0 * (G[2] + dt * Lk)
+            err = relerr(G[k + 1], ref)
+            if precision == eno.FP64:
+                assert err <= TOL64, (k, err)
+            else:
+                assert err <= TOL32_STEP, (k, err)
+                assert np.abs(G[k + 1] - ref).mean() / np.abs(ref).mean() <= TOL32_L1, k

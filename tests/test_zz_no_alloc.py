@@ -31,18 +31,19 @@ def _regular_step(shape_kw, U, dt):
         return s.get_state().reshape(U.shape)
 
 
-@pytest.mark.parametrize("system,order,precision,n,bc", [
-    (eno.EULER, 5, eno.FP64, 2000, eno.TRANSMISSIVE),
-    (eno.EULER, 7, eno.FP32_BULK, 777, eno.TRANSMISSIVE),
-    (eno.SCALAR_ADVECTION, 5, eno.FP64, 200, eno.PERIODIC),
+@pytest.mark.parametrize("system,order,precision,n,bc,alpha_mode", [
+    (eno.EULER, 5, eno.FP64, 2000, eno.TRANSMISSIVE, eno.ALPHA_PER_STEP),
+    (eno.EULER, 7, eno.FP32_BULK, 777, eno.TRANSMISSIVE, eno.ALPHA_PER_STEP),
+    (eno.SCALAR_ADVECTION, 5, eno.FP64, 200, eno.PERIODIC, eno.ALPHA_PER_STEP),
+    (eno.EULER, 5, eno.FP64, 1000, eno.TRANSMISSIVE, eno.ALPHA_PER_STAGE),
 ])
-def test_noalloc_step_matches_regular_path_twice(system, order, precision, n, bc):
+def test_noalloc_step_matches_regular_path_twice(system, order, precision, n, bc, alpha_mode):
     import torch
     lo, hi = (0.0, 1.0) if system == eno.EULER else (-1.0, 1.0)
     kw = dict(shape=(n,), lo=(lo,), hi=(hi,), system=system, order=order, precision=precision,
-              bc=bc)
+              bc=bc, alpha_mode=alpha_mode)
     cfg = eno.make_config((n,), (lo,), (hi,), system=system, order=order, precision=precision,
-                          bc=bc)
+                          bc=bc, alpha_mode=alpha_mode)
     if system == eno.EULER:
         U = inputs.euler1d_riemann(n, seed=11).reshape(3, n)
         dt = 0.2 / n
