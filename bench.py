@@ -503,6 +503,55 @@ def run_small(args, workload):
            "fp64": out["fp64"], "note": "launch-bound: whole run timed on the host clock"})
 
 
+def run_tie_study(args):
+    """FP32-bulk near-tie margin study: for each tie_rel, the stencil choices of
+    the FP32-bulk path against the FP64 path (itself oracle-identical) on
+    evolved 2D four-quadrant data, the FP64 re-decisions per step and the step
+    time."""
+    import torch
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    n, before = args.tie_n, args.tie_evolve
+    U = inputs.euler2d_quadrants(n, n, seed=1)
+    kw = dict(system=eno.EULER, order=5)
+    with eno.Solver((n, n), (0.0, 0.0), (1.0, 1.0), **kw) as s:
+        s.init_state(U)
+        s.advance_steps(before, 0.5)
+        Ue = s.get_state()
+        ref = [s.reconstruct_fluxes(d, want_idx=True)[1] for d in range(2)]
+    rows = []
+    for tr in (1e-2, 1e-3, 1e-4, 1e-5, 0.0):
+        with eno.Solver((n, n), (0.0, 0.0), (1.0, 1.0), precision=eno.FP32_BULK, tie_rel=tr,
+                        **kw) as s:
+            s.init_state(Ue)
+            f0 = s.stats().fp64_fallbacks
+            dis = tot = 0
+            for d in range(2):
+                _, idx = s.reconstruct_fluxes(d, want_idx=True)
+                dis += int((idx != ref[d]).sum())
+                tot += int(idx.size)
+            f1 = s.stats().fp64_fallbacks
+            s.init_state(Ue)
+            s.advance_steps(2, 0.5)
+            torch.cuda.synchronize()
+            f2 = s.stats().fp64_fallbacks
+            t0 = time.perf_counter()
+            s.advance_steps(args.steps, 0.5)
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / args.steps
+            f3 = s.stats().fp64_fallbacks
+        rows.append({"tie_rel": tr, "choices": tot, "disagreements": dis,
+                     "agreement": 1.0 - dis / tot, "redecided_in_flux_pass": f1 - f0,
+                     "redecided_per_step": (f3 - f2) / args.steps, "ms_per_step": ms})
+    best = min(rows, key=lambda r: r["ms_per_step"])
+    cells = n * n
+    _line(f"tie-study-euler2d-{n}x{n}-evolved{before}", cells * 3 / (best["ms_per_step"] * 1e-3),
+          best["ms_per_step"], args.steps, 2,
+          {"config": {"workload": f"tie-study-euler2d-{n}x{n}-evolved{before}", "order": 5},
+           "tie_study": rows,
+           "note": "value: fastest tie_rel; agreement against the FP64 path on the same state"})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,7 +563,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="euler2d",
-                    choices=["euler2d", "batched", "euler3d", "euler1d", "advection"])
+                    choices=["euler2d", "batched", "euler3d", "euler1d", "advection",
+                             "tie-study"])
+    ap.add_argument("--tie-n", type=int, default=2048)
+    ap.add_argument("--tie-evolve", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-subset", type=int, default=128)
     ap.add_argument("--n3d", type=int, default=512)
@@ -528,6 +580,8 @@ def main():
         return run_euler3d(args)
     if args.workload in ("euler1d", "advection"):
         return run_small(args, args.workload)
+    if args.workload == "tie-study":
+        return run_tie_study(args)
     return run_gpu(args)
 
 
