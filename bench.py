@@ -503,6 +503,64 @@ def run_small(args, workload):
            "fp64": out["fp64"], "note": "launch-bound: whole run timed on the host clock"})
 
 
+def run_paper_cases(args):
+    """The paper's printed test cases (Sec. 4) at its resolutions and end times,
+    FP32 bulk and FP64: composite advection wave (dx = 1/200 on [-1, 1], t = 20),
+    Lax tube (dx = 1/100 on [0, 2], t = 0.26), Titarev-Toro (dx = 1/200 on
+    [-5, 5], t = 5), 2D Riemann configurations 1 and 2 (800 x 800 cells on
+    [-1, 1]^2, t = 1); ENO-AO5 and ENO-AO7.  Whole runs timed on the host clock
+    (the 1D cases are launch-bound)."""
+    import torch
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    n2 = args.paper_n2d
+    cases = [
+        ("composite-wave", inputs.composite_wave(400), (400,), (-1.0,), (1.0,),
+         eno.SCALAR_ADVECTION, eno.PERIODIC, 20.0),
+        ("lax", inputs.lax_tube(200), (200,), (0.0,), (2.0,), eno.EULER, eno.TRANSMISSIVE, 0.26),
+        ("titarev-toro", inputs.titarev_toro(2000), (2000,), (-5.0,), (5.0,), eno.EULER,
+         eno.TRANSMISSIVE, 5.0),
+        ("riemann2d-1", inputs.riemann2d(1, n2, n2), (n2, n2), (-1.0, -1.0), (1.0, 1.0),
+         eno.EULER, eno.TRANSMISSIVE, 1.0),
+        ("riemann2d-2", inputs.riemann2d(2, n2, n2), (n2, n2), (-1.0, -1.0), (1.0, 1.0),
+         eno.EULER, eno.TRANSMISSIVE, 1.0),
+    ]
+    rows = []
+    total_cs, total_s = 0.0, 0.0
+    for name, U, shape, lo, hi, system, bc, t_end in cases:
+        cells = int(np.prod(shape))
+        for order in (5, 7):
+            res = {}
+            for pname, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
+                with eno.Solver(shape, lo, hi, system=system, order=order, bc=bc,
+                                precision=prec) as s:
+                    s.init_state(U)
+                    s.advance_steps(1, CFL)     # graph capture outside the timed run
+                    s.init_state(U)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    t, k = s.advance(t_end, cfl=CFL)
+                    sec = time.perf_counter() - t0
+                    res[pname] = (s.get_state(), k, sec, t)
+            a, b = res["fp32_bulk"][0], res["fp64"][0]
+            row = {"case": name, "order": order, "cells": cells, "t_end": t_end,
+                   "steps": res["fp32_bulk"][1],
+                   "fp32_bulk_cell_stage_per_s": cells * 3 * res["fp32_bulk"][1] / res["fp32_bulk"][2],
+                   "fp64_cell_stage_per_s": cells * 3 * res["fp64"][1] / res["fp64"][2],
+                   "fp32_bulk_seconds": res["fp32_bulk"][2], "fp64_seconds": res["fp64"][2],
+                   "l1_rel_fp32_bulk_vs_fp64": float(np.abs(a - b).mean() / np.abs(b).mean())}
+            if bc == eno.PERIODIC:
+                row["conservation_rel_fp64"] = float(abs(b.sum() - U.sum()) / np.abs(U).sum())
+            if system == eno.EULER:
+                row["min_density_fp64"] = float(b[0].min())
+            rows.append(row)
+            total_cs += cells * 3 * res["fp32_bulk"][1]
+            total_s += res["fp32_bulk"][2]
+    _line(f"paper-cases-riemann2d-{n2}", total_cs / total_s, 1e3 * total_s, len(rows), 1,
+          {"config": {"workload": f"paper-cases (Sec. 4), 2D at {n2}x{n2}"}, "cases": rows,
+           "note": "value: all FP32-bulk runs together, cell-stage updates per host second"})
+
+
 def run_tie_study(args):
     """FP32-bulk near-tie margin study: for each tie_rel, the stencil choices of
     the FP32-bulk path against the FP64 path (itself oracle-identical) on
@@ -564,7 +622,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="euler2d",
                     choices=["euler2d", "batched", "euler3d", "euler1d", "advection",
-                             "tie-study"])
+                             "tie-study", "paper-cases"])
+    ap.add_argument("--paper-n2d", type=int, default=800)
     ap.add_argument("--tie-n", type=int, default=2048)
     ap.add_argument("--tie-evolve", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=200)
@@ -582,6 +641,8 @@ def main():
         return run_small(args, args.workload)
     if args.workload == "tie-study":
         return run_tie_study(args)
+    if args.workload == "paper-cases":
+        return run_paper_cases(args)
     return run_gpu(args)
 
 
