@@ -584,6 +584,78 @@ __device__ __forceinline__ int redo_group(const SweepArgs& A, const TileGeo& g, 
   return pick;
 }
 
+// The same FP64 re-decision by one thread alone: it walks the window cell by
+// cell (two states live at a time).  Used when a warp has many flagged
+// choices at once, so that all lanes work on their own choices in parallel
+// instead of the warp serving them a few at a time.
+template <int NV, int ORDER, bool COHERENT>
+__device__ __forceinline__ int redo_lane(const SweepArgs& A, const TileGeo& g, int a, long long sj,
+                                         int v, int sgn, double alpha) {
+  using GE = Geo<ORDER>;
+  constexpr int G = GE::G;
+  const double gm1 = A.gamma - 1.0;
+  const long long line = g.base + (g.a0 + a) * g.stride_a;
+  // window cell r (0..2G-1) is cell sj - G + 1 + r of the line; the face lies
+  // between cells G-1 and G
+  auto load_cell = [&](int r, double (&q)[NV]) {
+    load_state<NV, COHERENT>(A.u_in, A.cstride, line + bc_map(sj - G + 1 + r, g.nd, A.bc) * g.stride_d,
+                             A.dir, q);
+  };
+  double L[NV];
+  if constexpr (NV > 1) {
+    double ql[NV], qr[NV], pl[NV], prr[NV];
+    load_cell(G - 1, ql);
+    load_cell(G, qr);
+    roe_prims<NV, double>(ql, gm1, pl);
+    roe_prims<NV, double>(qr, gm1, prr);
+    Eigen<NV, double> E;
+    roe_eigen<NV, double>(pl, prr, gm1, E);
+    left_row<NV, double>(E, v, L);
+  } else {
+    L[0] = 1.0;
+  }
+  const double sa = sgn == 0 ? alpha : -alpha;
+  // d[i] is difference k = i + G - 5 (sign 0) or G + 3 - i (sign 1, negated),
+  // between window cells k and k+1; consecutive i share one cell
+  double d[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = 0.0;
+  double qlo[NV], qhi[NV];
+  {
+    const int k0 = sgn == 0 ? GE::LO + G - 5 : G + 3 - GE::LO;
+    load_cell(k0, qlo);
+    load_cell(k0 + 1, qhi);
+  }
+#pragma unroll
+  for (int i = GE::LO; i <= GE::HI; ++i) {
+    double dq[NV], dF[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) dq[c] = qhi[c] - qlo[c];
+    flux_diff<NV, double>(qlo, qhi, dq, gm1, A.adv_speed, dF);
+    double w = 0.0;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) w += L[c] * (0.5 * (dF[c] + sa * dq[c]));
+    d[i] = sgn == 0 ? w : -w;
+    if (i < GE::HI) {
+      const int k = sgn == 0 ? i + G - 5 : G + 3 - i;
+      if (sgn == 0) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) qlo[c] = qhi[c];
+        load_cell(k + 2, qhi);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) qhi[c] = qlo[c];
+        load_cell(k - 1, qlo);
+      }
+    }
+  }
+  int pick;
+  bool m;
+  const double nomx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  eno_select<ORDER, double, false>(d, A.delta, 0.0, nomx, 0.0, pick, m);
+  return pick;
+}
+
 // Position of the n-th (0-based) set bit of x, or -1.
 __device__ __forceinline__ int nth_set_bit(unsigned x, int n) {
   for (int i = 0; i < n && x; ++i) x &= x - 1;
@@ -910,6 +982,22 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       constexpr int NG = 32 / W;
       unsigned todo = fix;
       unsigned long long picks = 0ull;
+      // Many flags in the warp: each lane re-decides its own choices alone
+      // (as many rounds as the busiest lane has flags) instead of the warp
+      // serving NG choices per pass; a lone re-decision costs about 2.5x
+      // (ENO-AO5) or 3x (ENO-AO7) a cooperative pass.
+      const unsigned total = __reduce_add_sync(FULL, (unsigned)__popc(fix));
+      const unsigned most = __reduce_max_sync(FULL, (unsigned)__popc(fix));
+      if (most * (ORDER == 7 ? 6u : 5u) < 2u * ((total + NG - 1) / NG)) {
+        while (todo) {
+          const int kk = __ffs(todo) - 1;
+          todo &= todo - 1;
+          const int pick = redo_lane<NV, ORDER, COHERENT>(A, g, al, g.s0 + f - 1, kk >> 1, kk & 1,
+                                                          alpha_d);
+          picks |= (unsigned long long)pick << (4 * kk);
+          ++nfall;
+        }
+      }
       for (int pass = 0; pass < 64 * NV + 1; ++pass) {
         const unsigned have = __ballot_sync(FULL, todo != 0u);
         if (!have) break;
