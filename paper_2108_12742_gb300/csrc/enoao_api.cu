@@ -66,16 +66,17 @@ __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
     const double rho = U[i];
+    const double ir = 1.0 / rho;  // one FP64 division per cell (GB300's FP64 unit is slow)
     double m2 = 0.0;
     for (int c = 1; c < nv - 1; ++c) m2 += U[c * ncell + i] * U[c * ncell + i];
-    const double p = (gamma - 1.0) * (U[(nv - 1) * ncell + i] - 0.5 * m2 / rho);
+    const double p = (gamma - 1.0) * (U[(nv - 1) * ncell + i] - 0.5 * m2 * ir);
     if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p)) {
       atomicOr(&st->err, kErrNonPhys);
       atomicMin(&st->err_cell, i);
       continue;
     }
-    const double cs = sqrt(gamma * p / rho);
-    for (int d = 0; d < ndim; ++d) amax[d] = fmax(amax[d], fabs(U[(1 + d) * ncell + i] / rho) + cs);
+    const double cs = sqrt(gamma * p * ir);
+    for (int d = 0; d < ndim; ++d) amax[d] = fmax(amax[d], fabs(U[(1 + d) * ncell + i]) * ir + cs);
   }
   __shared__ double red[3][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -1175,18 +1175,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         // depend on FP32 rounding of the splitting constant.
         if constexpr (NV > 1) {
           if (A.stage < 2 && (mode & kModeAlpha)) {
-            const double rho = unew[0];
+            const double rho = unew[0], ir = 1.0 / rho;
             double m2 = 0.0;
 #pragma unroll
             for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
-            const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 / rho);
+            const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 * ir);
             if (!(rho > 0.0 && p > 0.0 && isfinite(p))) {
               atomicOr(&st->err, kErrNonPhys);
               atomicMin(&st->err_cell, cell);
             } else {
-              const double cs = sqrt(A.gamma * p / rho);
+              const double cs = sqrt(A.gamma * p * ir);
 #pragma unroll
-              for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
+              for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
             }
             return;
           }
@@ -1223,19 +1223,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
       } else if constexpr (NV > 1) {
         // non-physical check and next-step alpha on the new state
-        const double rho = unew[0];
+        const double rho = unew[0], ir = 1.0 / rho;  // one FP64 division per cell
         double m2 = 0.0;
 #pragma unroll
         for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
-        const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 / rho);
+        const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 * ir);
         const bool ok = rho > 0.0 && p > 0.0 && isfinite(p);
         if (!ok) {
           atomicOr(&st->err, kErrNonPhys);
           atomicMin(&st->err_cell, cell);
         } else if (mode & kModeAlpha) {
-          const double cs = sqrt(A.gamma * p / rho);
+          const double cs = sqrt(A.gamma * p * ir);
 #pragma unroll
-          for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d] / rho) + cs);
+          for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
         }
       } else {
         if (!isfinite(unew[0])) {
