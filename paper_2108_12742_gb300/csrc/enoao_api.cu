@@ -226,8 +226,8 @@ void default_tiles(enoao_ctx* c) {
       c->ta[d] = c->cfg.ndim == 1 ? 1 : 4;
       c->ts[d] = 63;
     } else {
-      c->ta[d] = f32 ? 16 : 32;
-      c->ts[d] = f32 ? 23 : 15;  // FP32 2D Euler: six 36 KB blocks per SM
+      c->ta[d] = f32 ? 8 : 32;
+      c->ts[d] = f32 ? 47 : 15;  // FP32 2D Euler: six 30 KB blocks per SM, 17 % halo
     }
     c->block[d] = 128;
   }
@@ -236,8 +236,8 @@ void default_tiles(enoao_ctx* c) {
 enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
   if (ta < 1 || ts < 1 || ta * ts > 8192)
     return fail(c, ENOAO_EINVAL, "tile %dx%d out of range", ta, ts);
-  if (d > 0 && ta != 32 && ta != 16 && ta != 64)
-    return fail(c, ENOAO_EINVAL, "axis %d needs 16, 32 or 64 lines per tile", d);
+  if (d > 0 && ta != 8 && ta != 16 && ta != 32 && ta != 64)
+    return fail(c, ENOAO_EINVAL, "axis %d needs 8, 16, 32 or 64 lines per tile", d);
   if (d == 0 && ta != 1 && ta != 2 && ta != 4 && ta != 8)
     return fail(c, ENOAO_EINVAL, "axis 0 needs 1, 2, 4 or 8 lines per tile");
   size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), ta, ts,
@@ -829,8 +829,8 @@ enoao_status enoao_autotune(enoao_ctx* c) {
         for (int ts : tss)
           if (c->cfg.ndim > 1 || ta == 1) cands.push_back({ta, ts});
     } else {
-      const int tas[] = {16, 32, 64};
-      const int tss[] = {7, 15, 23, 31, 63};
+      const int tas[] = {8, 16, 32, 64};
+      const int tss[] = {7, 15, 23, 31, 47, 63};
       for (int ta : tas)
         for (int ts : tss) cands.push_back({ta, ts});
     }

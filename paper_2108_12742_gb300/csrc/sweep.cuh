@@ -737,6 +737,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const int dir = A.dir;
   const bool sfast = dir == 0;
   const R alpha = (R)alpha_d;
+  const R halpha = R(0.5) * alpha;
   const R gm1 = (R)(A.gamma - 1.0);
   const R adv = (R)A.adv_speed;
   const R delta = (R)A.delta;
@@ -858,11 +859,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
         }
         flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
+        // (dF +- alpha dq)/2 as dF/2 +- (alpha/2) dq: the same bits (halving is
+        // exact), one multiplication per component fewer
         R fp[NV], fm[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
-          fp[c] = R(0.5) * (dF[c] + alpha * dq[c]);
-          fm[c] = R(0.5) * (dF[c] - alpha * dq[c]);
+          const R hdF = R(0.5) * dF[c];
+          fp[c] = fma(halpha, dq[c], hdF);
+          fm[c] = fma(-halpha, dq[c], hdF);
         }
         CV::store(dfp, cells, si, fp);
         CV::store(dfm, cells, si, fm);
