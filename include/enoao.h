@@ -193,6 +193,29 @@ int enoao_launches_per_step(const enoao_ctx *ctx);
 enoao_status enoao_set_tiles(enoao_ctx *ctx, int dir, int ta, int ts);
 enoao_status enoao_get_tiles(const enoao_ctx *ctx, int dir, int *ta, int *ts);
 
+/* Where FP32_BULK re-decides its near-tie stencil choices in FP64 (the
+ * selection of Sec. 3.2 taken again from the FP64 state when the FP32
+ * indicators cannot order it).  IN_SWEEP: inside the sweep, by the tile that
+ * meets the choice.  GRID: each sweep lists the faces with such choices and a
+ * pass over the whole GPU re-decides them after it, then applies the changed
+ * choices to the two cells of each face (two extra launches per sweep; the
+ * choices cluster at discontinuities, in tiles whose SMs would otherwise set
+ * the sweep's length).  GRID pays where near-ties reach a few per cent of
+ * the cells per step (shock and slip-line dominated flows such as the 2D
+ * Riemann problems); elsewhere the pass, which has no FP32 work to hide its
+ * FP64 work behind, costs more than it saves.  AUTO (default): IN_SWEEP.
+ * Both give the same choices; the state differs by FP32 rounding of the
+ * correction.  Either way results do not depend on tile shapes.  GRID needs
+ * 8 + 4 nv + 4 bytes per face of the axis with most faces, allocated here.
+ * The FP64 precision has no near-ties and ignores the mode.  GRID on a grid
+ * with 2^32 or more faces along an axis falls back to IN_SWEEP.
+ * Errors: ENOAO_EINVAL for an unknown mode or GRID on a batched context,
+ * ENOAO_ENOMEM when the list cannot be allocated (the mode is then kept). */
+enum { ENOAO_REDECIDE_AUTO = 0, ENOAO_REDECIDE_IN_SWEEP = 1, ENOAO_REDECIDE_GRID = 2 };
+enoao_status enoao_set_redecide(enoao_ctx *ctx, int mode);
+/* 1 when the context's steps use the grid-wide pass, else 0. */
+int enoao_uses_grid_redecide(const enoao_ctx *ctx);
+
 /* One third-order TVD Runge-Kutta step of a 1D problem that allocates no
  * device memory.  The paper has no counterpart: this is a deployment aid for
  * callers that cannot let a library allocate -- applications that reserve

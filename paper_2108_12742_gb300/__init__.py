@@ -26,6 +26,7 @@ SCALAR_ADVECTION, EULER = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 FP64, FP32_BULK = 0, 1
 ALPHA_PER_STEP, ALPHA_PER_STAGE = 0, 1
+REDECIDE_AUTO, REDECIDE_IN_SWEEP, REDECIDE_GRID = 0, 1, 2
 
 STATUS = {0: "ENOAO_OK", 1: "ENOAO_EINVAL", 2: "ENOAO_ENOMEM", 3: "ENOAO_ECUDA",
           4: "ENOAO_ENONPHYS", 5: "ENOAO_ETIMEOUT"}
@@ -96,6 +97,8 @@ def load():
         "enoao_get_stats": (ctypes.c_int, [P, ctypes.POINTER(Stats)]),
         "enoao_launches_per_step": (ctypes.c_int, [P]),
         "enoao_set_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "enoao_set_redecide": (ctypes.c_int, [P, ctypes.c_int]),
+        "enoao_uses_grid_redecide": (ctypes.c_int, [P]),
         "enoao_get_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
         "enoao_autotune": (ctypes.c_int, [P]),
@@ -270,6 +273,14 @@ class Solver:
 
     def set_tiles(self, d, ta, ts):
         self._check(self._lib.enoao_set_tiles(self._h, d, ta, ts))
+
+    def set_redecide(self, mode):
+        """Where FP32-bulk near-ties are re-decided in FP64: REDECIDE_AUTO,
+        REDECIDE_IN_SWEEP or REDECIDE_GRID (the grid-wide pass after each sweep)."""
+        self._check(self._lib.enoao_set_redecide(self._h, mode))
+
+    def uses_grid_redecide(self):
+        return bool(self._lib.enoao_uses_grid_redecide(self._h))
 
     def get_tiles(self, d):
         a, b = ctypes.c_int(), ctypes.c_int()

@@ -247,10 +247,57 @@ enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
   return ENOAO_OK;
 }
 
+// FP32 bulk stepping: whether near-tie choices go to the grid-wide FP64
+// re-decision pass after each sweep instead of being re-decided inside the
+// sweep's tiles (enoao_set_redecide; AUTO currently re-decides in the sweep).
+bool use_list(const enoao_ctx* c) {
+  if (!fp32(c) || c->batch || c->redecide != ENOAO_REDECIDE_GRID) return false;
+  long long faces = 0;
+  for (int d = 0; d < c->cfg.ndim; ++d)
+    faces = std::max(faces, c->ncell / c->cfg.n[d] * (c->cfg.n[d] + 1));
+  return faces < (1ll << 32);  // list slots are counted in 32 bits
+}
+
+// Allocates the re-decision list when the context uses it: a slot per face of
+// the axis with the most faces (a sweep lists each face at most once).
+enoao_status ensure_list(enoao_ctx* c) {
+  if (!use_list(c) || c->redo) return ENOAO_OK;
+  long long cap = 0;
+  for (int d = 0; d < c->cfg.ndim; ++d)
+    cap = std::max(cap, c->ncell / c->cfg.n[d] * (c->cfg.n[d] + 1));
+  cudaError_t e = cudaMalloc(&c->redo, (size_t)cap * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&c->redo_dc, (size_t)cap * c->nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->redo_mark, (size_t)cap * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->redo_mark, 0, (size_t)cap * sizeof(unsigned), c->s);
+  if (e != cudaSuccess) {
+    cudaFree(c->redo);
+    cudaFree(c->redo_dc);
+    cudaFree(c->redo_mark);
+    c->redo = nullptr;
+    c->redo_dc = nullptr;
+    c->redo_mark = nullptr;
+    return fail(c, e == cudaErrorMemoryAllocation ? ENOAO_ENOMEM : ENOAO_ECUDA,
+                "re-decision list of %lld faces: %s", cap, cudaGetErrorString(e));
+  }
+  c->redo_cap = cap;
+  return ENOAO_OK;
+}
+
+// list: a stepping sweep (stage 0..2) of a context that uses the re-decision
+// list; the pass is launched right after the sweep (after recording
+// after_sweep, when given).
 enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double* u_in,
-                          double* u_out, double* fhat, int8_t* idx) {
+                          double* u_out, double* fhat, int8_t* idx, bool list = false,
+                          cudaEvent_t after_sweep = nullptr) {
   SweepArgs a;
   memset(&a, 0, sizeof a);
+  if (list) {
+    a.redo = c->redo;
+    a.redo_dc = c->redo_dc;
+    a.redo_mark = c->redo_mark;
+    a.redo_cap = c->redo_cap;
+    a.redo_coef = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  }
   a.u_in = u_in;
   a.u0 = c->U[0];
   a.u_out = u_out;
@@ -307,6 +354,11 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   e = fp32(c) ? sweep_launch_fp32(c->nv, c->cfg.order, a, (int)grid, block, smem, c->s)
               : sweep_launch_fp64(c->nv, c->cfg.order, a, (int)grid, block, smem, c->s);
   if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+  if (after_sweep) CU(c, cudaEventRecord(after_sweep, c->s));
+  if (list) {
+    e = redo_launch_fp32(c->nv, c->cfg.order, a, c->sms * 8, c->s);
+    if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "re-decision pass: %s", cudaGetErrorString(e));
+  }
   return ENOAO_OK;
 }
 
@@ -326,13 +378,15 @@ enoao_status enqueue_stage(enoao_ctx* c, int stage) {
   // alpha of the written state: for the next step (stage 2), or for the next
   // stage when each stage takes its own
   const bool want_alpha = stage == 2 || per_stage_alpha(c);
+  const bool list = use_list(c);
+  if (list && !c->redo) return fail(c, ENOAO_ENOMEM, "re-decision list not allocated");
   for (int d = 0; d < nd; ++d) {
     int mode;
     if (d < nd - 1)
       mode = kModeRhsStore | (d > 0 ? kModeRhsAdd : 0);
     else
       mode = kModeCombine | (nd > 1 ? kModeRhsAdd : 0) | (want_alpha ? kModeAlpha : 0);
-    enoao_status r = launch_sweep(c, d, stage, mode, in, out, nullptr, nullptr);
+    enoao_status r = launch_sweep(c, d, stage, mode, in, out, nullptr, nullptr, list);
     if (r != ENOAO_OK) return r;
   }
   return ENOAO_OK;
@@ -400,6 +454,8 @@ enoao_status check_err(enoao_ctx* c) {
     return fail(c, ENOAO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) at cell %lld",
                 (long long)c->st_host->err_cell);
   if (c->st_host->err & kErrTimeout) return fail(c, ENOAO_ETIMEOUT, "device wait timed out");
+  if (c->st_host->err & kErrRedoFull)
+    return fail(c, ENOAO_ECUDA, "internal error: re-decision list overflow");
   return ENOAO_OK;
 }
 
@@ -506,6 +562,12 @@ static enoao_status create_common(const enoao_config* cfg, void* stream, enoao_c
       return r;
     }
     default_tiles(c);
+    enoao_status r = ensure_list(c);
+    if (r != ENOAO_OK) {
+      g_create_error = c->err;
+      enoao_destroy(c);
+      return r;
+    }
   }
   reset_state_kernel<<<1, 1, 0, c->s>>>(c->st);
   e = cudaStreamSynchronize(c->s);
@@ -555,6 +617,9 @@ void enoao_destroy(enoao_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (int k = 0; k < 3; ++k) cudaFree(c->U[k]);
   cudaFree(c->rhs);
+  cudaFree(c->redo);
+  cudaFree(c->redo_dc);
+  cudaFree(c->redo_mark);
   cudaFree(c->st);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->ev_a) cudaEventDestroy(c->ev_a);
@@ -760,8 +825,30 @@ enoao_status enoao_get_stats(enoao_ctx* c, enoao_stats* out) {
 int enoao_launches_per_step(const enoao_ctx* c) {
   if (!c) return 0;
   if (c->batch) return 0;  // one persistent launch covers every step
-  return 1 + 3 * c->cfg.ndim + (per_stage_alpha(c) ? 2 : 0);
+  return 1 + 3 * c->cfg.ndim * (use_list(c) ? 3 : 1) + (per_stage_alpha(c) ? 2 : 0);
 }
+
+enoao_status enoao_set_redecide(enoao_ctx* c, int mode) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (mode != ENOAO_REDECIDE_AUTO && mode != ENOAO_REDECIDE_IN_SWEEP && mode != ENOAO_REDECIDE_GRID)
+    return fail(c, ENOAO_EINVAL, "re-decision mode must be AUTO, IN_SWEEP or GRID");
+  if (c->batch && mode == ENOAO_REDECIDE_GRID)
+    return fail(c, ENOAO_EINVAL, "batched contexts re-decide inside the sweep");
+  const int prev = c->redecide;
+  c->redecide = mode;
+  enoao_status r = ensure_list(c);
+  if (r != ENOAO_OK) {
+    c->redecide = prev;
+    return r;
+  }
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return ENOAO_OK;
+}
+
+int enoao_uses_grid_redecide(const enoao_ctx* c) { return c && use_list(c) ? 1 : 0; }
 
 enoao_status enoao_set_tiles(enoao_ctx* c, int dir, int ta, int ts) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
@@ -797,16 +884,22 @@ enoao_status enoao_time_sweep(enoao_ctx* c, int dir, int nrep, float* ms) {
   const int nd = c->cfg.ndim;
   const int mode = dir < nd - 1 ? (kModeRhsStore | (dir > 0 ? kModeRhsAdd : 0))
                                 : (kModeCombine | (nd > 1 ? kModeRhsAdd : 0));
-  r = launch_sweep(c, dir, 0, mode, c->U[0], c->U[1], nullptr, nullptr);  // warm-up
+  // the sweep as steps launch it (with the re-decision pass after it, when
+  // the context uses one; only the sweep kernel is timed)
+  const bool list = use_list(c);
+  r = launch_sweep(c, dir, 0, mode, c->U[0], c->U[1], nullptr, nullptr, list);  // warm-up
   if (r != ENOAO_OK) return r;
-  CU(c, cudaEventRecord(c->t0, c->s));
-  for (int k = 0; k < nrep && r == ENOAO_OK; ++k)
-    r = launch_sweep(c, dir, 0, mode, c->U[0], c->U[1], nullptr, nullptr);
-  if (r != ENOAO_OK) return r;
-  CU(c, cudaEventRecord(c->t1, c->s));
-  CU(c, cudaEventSynchronize(c->t1));
   float total = 0.f;
-  CU(c, cudaEventElapsedTime(&total, c->t0, c->t1));
+  for (int k = 0; k < nrep && r == ENOAO_OK; ++k) {
+    CU(c, cudaEventRecord(c->t0, c->s));
+    r = launch_sweep(c, dir, 0, mode, c->U[0], c->U[1], nullptr, nullptr, list, c->t1);
+    if (r != ENOAO_OK) return r;
+    CU(c, cudaEventSynchronize(c->t1));
+    float one = 0.f;
+    CU(c, cudaEventElapsedTime(&one, c->t0, c->t1));
+    total += one;
+  }
+  CU(c, cudaStreamSynchronize(c->s));
   *ms = total / nrep;
   return leave(c);
 }
@@ -820,6 +913,7 @@ enoao_status enoao_autotune(enoao_ctx* c) {
   if (r != ENOAO_OK) return r;
   CU(c, cudaMemcpyAsync(c->U[2], c->U[0], bytes, cudaMemcpyDeviceToDevice, c->s));
   const bool f32 = fp32(c);
+  const bool list = use_list(c);  // candidates timed with the pass steps launch after them
   for (int d = 0; d < c->cfg.ndim; ++d) {
     std::vector<std::pair<int, int>> cands;
     if (d == 0) {
@@ -843,10 +937,11 @@ enoao_status enoao_autotune(enoao_ctx* c) {
       c->ts[d] = p.second;
       const int mode = kModeCombine;  // stage 0 into U1; the live state U^n is untouched
       alpha_current_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
-      r = launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr);  // warm-up
+      r = launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr, list);  // warm-up
       if (r != ENOAO_OK) continue;
       CU(c, cudaEventRecord(c->t0, c->s));
-      for (int k = 0; k < 3; ++k) launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr);
+      for (int k = 0; k < 3; ++k)
+        launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr, list);
       CU(c, cudaEventRecord(c->t1, c->s));
       CU(c, cudaEventSynchronize(c->t1));
       float ms = 0.f;

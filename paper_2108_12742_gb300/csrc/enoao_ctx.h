@@ -39,4 +39,10 @@ struct enoao_ctx {
   std::string err;
   enoao::BatchState* batch = nullptr;
   int device = 0;
+  // FP32 bulk: faces listed for the grid-wide FP64 re-decision pass
+  int redecide = ENOAO_REDECIDE_AUTO;
+  unsigned long long* redo = nullptr;  // a slot per face of the axis with most faces
+  float* redo_dc = nullptr;            // nv per slot
+  unsigned* redo_mark = nullptr;       // per face
+  long long redo_cap = 0;
 };

@@ -26,19 +26,23 @@ struct StepState {
   unsigned long long alpha_acc[2][3];  // running max of |u_d| + c (bit patterns);
                                        // step n reads [n % 2], its last stage fills [par]
   int par;                  // alpha_acc slot the current step's last stage fills
-  int err;                  // error bits (kErrNonPhys, kErrTimeout)
+  int err;                  // error bits (kErrNonPhys, kErrTimeout, kErrRedoFull)
   long long err_cell;       // first cell (min index) that raised kErrNonPhys
   unsigned long long fallbacks;  // FP32-bulk decisions re-done in FP64
   unsigned long long decisions;  // stencil decisions taken
   unsigned long long tile_next;  // dynamic tile queue of the running sweep launch
   unsigned int blocks_done;      // blocks of the running sweep launch that have left it
-  unsigned int pad2;
+  unsigned int redo_n;            // faces listed for FP64 re-decision by the running sweep
   unsigned long long alpha_stage[3];  // per-stage alpha: running max over the
                                       // state stage 0 or 1 writes (bit patterns)
+  unsigned int redo_epoch;        // sweeps that listed faces: tags the changed-face marks
+  unsigned int redo_done;         // blocks of the running apply pass that have left it
 };
+
 
 constexpr int kErrNonPhys = 1;
 constexpr int kErrTimeout = 2;
+constexpr int kErrRedoFull = 4;  // re-decision list full (cannot happen: one slot per face)
 
 // Modes of a sweep launch (bit set).
 constexpr int kModeRhsStore = 1;   // write this axis' L(u) into rhs
@@ -55,6 +59,14 @@ struct SweepArgs {
   void* rhs;            // accumulated L(u) of earlier axes ([nv][N], bulk type)
   double* fhat;         // kModeFlux: interface fluxes [nv][faces]
   int8_t* idx_out;      // kModeFlux: choices [nv][2][faces] (nullable)
+  unsigned long long* redo;  // FP32 bulk, stepping: faces listed for the grid-wide FP64
+                        // re-decision pass (face index << 16 | flagged choices, bit
+                        // field * 2 + sign), a slot per face of the axis; null: the
+                        // sweep re-decides its near-ties itself
+  float* redo_dc;       // per listed face: change of its correction C (nv, sweep order)
+  unsigned* redo_mark;  // per face of the axis: redo_epoch when its correction changed
+  double redo_coef;     // weight of dt L(u) in the stage's combine (1, 1/4, 2/3)
+  long long redo_cap;   // slots of redo
   StepState* st;
   long long n[3];       // cells per axis
   long long ncell;      // total cells
@@ -92,6 +104,7 @@ cudaError_t sweep_configure_fp64(int nv, int order, size_t smem);
 cudaError_t sweep_configure_fp32(int nv, int order, size_t smem);
 cudaError_t sweep_occupancy_fp64(int nv, int order, int block, size_t smem, int* per_sm);
 cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm);
+cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cudaStream_t s);
 
 // Raises a kernel's dynamic shared-memory limit to at least smem, never
 // lowers it: the limit belongs to the kernel, not to one launch, and the

@@ -712,10 +712,94 @@ struct CellVec {
   }
 };
 
+// Lax-Friedrichs split differences of one pair of neighbouring cells in the
+// bulk precision (phase 1): dq = qb - qa rounded once from FP64, the flux
+// difference in difference form, and (dF +- alpha dq)/2 written as
+// dF/2 +- (alpha/2) dq (the same bits: halving is exact).
+template <int NV, typename R>
+__device__ __forceinline__ void split_diff(const double (&qa64)[NV], const double (&qb64)[NV],
+                                           const R (&qa)[NV], R gm1, R adv, R halpha,
+                                           R (&fp)[NV], R (&fm)[NV]) {
+  R qb[NV], dq[NV], dF[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    qb[c] = to_bulk<R>(qb64[c]);
+    dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
+  }
+  flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    const R hdF = R(0.5) * dF[c];
+    fp[c] = fma(halpha, dq[c], hdF);
+    fm[c] = fma(-halpha, dq[c], hdF);
+  }
+}
+
+// FP32 bulk: the state is checked, and the next step's alpha taken, on each
+// step's final state; the kinetic energy, sound speed and |u| + c are FP32,
+// the energy difference E - ke stays FP64.  The alpha of a later stage of the
+// same step (per-stage alpha) is taken in FP64 like the FP64 path's: the
+// stage's stencil choices must not depend on FP32 rounding of the splitting
+// constant.  unew is the combined state of cell in conserved order.
+template <int NV>
+__device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long cell,
+                                                 const double (&unew)[NV], int mode,
+                                                 double (&amax)[3]) {
+  StepState* st = A.st;
+  if constexpr (NV > 1) {
+    if (A.stage < 2 && (mode & kModeAlpha)) {
+      const double rho = unew[0], ir = 1.0 / rho;
+      double m2 = 0.0;
+#pragma unroll
+      for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
+      const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 * ir);
+      if (!(rho > 0.0 && p > 0.0 && isfinite(p))) {
+        atomicOr(&st->err, kErrNonPhys);
+        atomicMin(&st->err_cell, cell);
+      } else {
+        const double cs = sqrt(A.gamma * p * ir);
+#pragma unroll
+        for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
+      }
+      return;
+    }
+  }
+  if (A.stage == 2) {
+    if constexpr (NV > 1) {
+      const float rho = f32_rn(unew[0]);
+      float m2 = 0.0f;
+#pragma unroll
+      for (int c = 1; c < NV - 1; ++c) {
+        const float m = f32_rn(unew[c]);
+        m2 += m * m;
+      }
+      const float ke = __fdividef(0.5f * m2, rho);
+      const float p = f32_rn((A.gamma - 1.0) * (unew[NV - 1] - f64_of(ke)));
+      const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
+      if (!ok) {
+        atomicOr(&st->err, kErrNonPhys);
+        atomicMin(&st->err_cell, cell);
+      } else if (mode & kModeAlpha) {
+        const float ir = __fdividef(1.0f, rho);
+        const float cs = sqrtf((float)A.gamma * p * ir);
+#pragma unroll
+        for (int d = 0; d < NV - 2; ++d) {
+          // non-negative: the bit patterns order like the values
+          const double s = f64_of(fabsf(f32_rn(unew[1 + d])) * ir + cs);
+          if (okey(s) > okey(amax[d])) amax[d] = s;
+        }
+      }
+    } else if (!isfinite(unew[0])) {
+      atomicOr(&st->err, kErrNonPhys);
+      atomicMin(&st->err_cell, cell);
+    }
+  }
+}
+
 // One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
 // constant of the swept axis and the step size; amax accumulates |u_d| + c of
 // combined states (last stage), nfall counts FP64 re-decisions.
-template <int NV, int ORDER, typename R, bool COHERENT = false>
+template <int NV, int ORDER, typename R, bool COHERENT = false, bool DEFER = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
                                            unsigned char* smem_raw, double alpha_d, double dt,
                                            double (&amax)[3], unsigned long long& nfall) {
@@ -745,7 +829,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
   const R inv_dx_r = (R)inv_dx;
-  const float gamma_f = (float)A.gamma;
   // Shared-memory rows of SE cells per line for every axis: unit stride
   // along the swept axis (window offsets are immediates); SE is odd, so the
   // y/z sweeps, whose lanes run across lines, hit distinct banks.
@@ -852,22 +935,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         const long long sb = bc_map(g.s0 - G + e + 1, g.nd, A.bc);
         double qb64[NV];
         load_state<NV, COHERENT>(A.u_in, A.cstride, la + sb * g.stride_d, dir, qb64);
-        R qb[NV], dq[NV], dF[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          qb[c] = to_bulk<R>(qb64[c]);
-          dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
-        }
-        flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
-        // (dF +- alpha dq)/2 as dF/2 +- (alpha/2) dq: the same bits (halving is
-        // exact), one multiplication per component fewer
         R fp[NV], fm[NV];
-#pragma unroll
-        for (int c = 0; c < NV; ++c) {
-          const R hdF = R(0.5) * dF[c];
-          fp[c] = fma(halpha, dq[c], hdF);
-          fm[c] = fma(-halpha, dq[c], hdF);
-        }
+        split_diff<NV, R>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
         CV::store(dfp, cells, si, fp);
         CV::store(dfm, cells, si, fm);
       }
@@ -916,7 +985,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
                                               pick, marg);
           if constexpr (FP32) {
-            if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 in phase 2b
+            if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 (phase 2b or the pass)
           }
           if ((mode & kModeFlux) && A.idx_out && own) {
             const long long nf = A.ncell / g.nd * (g.nd + 1);
@@ -950,12 +1019,32 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   }
   __syncthreads();
 
-  // ---------------- phase 2b (FP32 bulk): FP64 re-decision of near-ties
+  // ---------------- phase 2b (FP32 bulk, re-decision list): list the faces
+  // with flagged choices that this tile owns; the grid-wide pass corrects both
+  // cells of each, whichever tiles they lie in, so results do not depend on
+  // tiles.  Nothing here changes Cf: phase 3 uses the FP32 choices.
+  if constexpr (FP32 && DEFER) {
+    for_items(lgTA, nts + 1, sfast, [&](const int a, const int f) {
+      if (g.a0 + a >= g.na) return;
+      const unsigned fix = fixmask[sidx(a, G - 1 + f)];
+      const long long gface = g.s0 + f;
+      if (!fix || !((gface <= g.nd) && (f < A.ts || gface == g.nd))) return;
+      const unsigned slot = atomicAdd(&st->redo_n, 1u);
+      if (slot < A.redo_cap) {
+        const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+        A.redo[slot] = ((unsigned long long)fc << 16) | fix;
+      } else {
+        atomicOr(&st->err, kErrRedoFull);
+      }
+    });
+  }
+
+  // ---------------- phase 2b (FP32 bulk, no list): FP64 re-decision of near-ties
   // Flagged choices are re-decided from the FP64 state by lane groups of the
   // warp (redo_group), then each face applies the changes of its chosen values
   // to its correction in a fixed field/sign order.  Kept out of phase 2 so the
   // rare FP64 path does not raise the register footprint of the common one.
-  if constexpr (FP32) {
+  if constexpr (FP32 && !DEFER) {
     constexpr int W = 2 * G <= 8 ? 8 : 16;  // lanes per re-decision group
     const unsigned FULL = 0xffffffffu;
     const int cnt = nts + 1;
@@ -1171,60 +1260,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
       for (int k = 0; k < NV; ++k) unew[k] = comp_of<NV>(up, k, dir);  // conserved order
       if constexpr (FP32) {
-        // FP32 bulk: the state is checked, and the next step's alpha taken,
-        // on each step's final state; the kinetic energy, sound speed and
-        // |u| + c are FP32, the energy difference E - ke stays FP64.  The
-        // alpha of a later stage of the same step (per-stage alpha) is taken
-        // in FP64 like the FP64 path's: the stage's stencil choices must not
-        // depend on FP32 rounding of the splitting constant.
-        if constexpr (NV > 1) {
-          if (A.stage < 2 && (mode & kModeAlpha)) {
-            const double rho = unew[0], ir = 1.0 / rho;
-            double m2 = 0.0;
-#pragma unroll
-            for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
-            const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 * ir);
-            if (!(rho > 0.0 && p > 0.0 && isfinite(p))) {
-              atomicOr(&st->err, kErrNonPhys);
-              atomicMin(&st->err_cell, cell);
-            } else {
-              const double cs = sqrt(A.gamma * p * ir);
-#pragma unroll
-              for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
-            }
-            return;
-          }
-        }
-        if (A.stage == 2) {
-          if constexpr (NV > 1) {
-            const float rho = f32_rn(unew[0]);
-            float m2 = 0.0f;
-#pragma unroll
-            for (int c = 1; c < NV - 1; ++c) {
-              const float m = f32_rn(unew[c]);
-              m2 += m * m;
-            }
-            const float ke = __fdividef(0.5f * m2, rho);
-            const float p = f32_rn((A.gamma - 1.0) * (unew[NV - 1] - f64_of(ke)));
-            const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
-            if (!ok) {
-              atomicOr(&st->err, kErrNonPhys);
-              atomicMin(&st->err_cell, cell);
-            } else if (mode & kModeAlpha) {
-              const float ir = __fdividef(1.0f, rho);
-              const float cs = sqrtf(gamma_f * p * ir);
-#pragma unroll
-              for (int d = 0; d < NV - 2; ++d) {
-                // non-negative: the bit patterns order like the values
-                const double s = f64_of(fabsf(f32_rn(unew[1 + d])) * ir + cs);
-                if (okey(s) > okey(amax[d])) amax[d] = s;
-              }
-            }
-          } else if (!isfinite(unew[0])) {
-            atomicOr(&st->err, kErrNonPhys);
-            atomicMin(&st->err_cell, cell);
-          }
-        }
+        bulk_state_check<NV>(A, cell, unew, mode, amax);
       } else if constexpr (NV > 1) {
         // non-physical check and next-step alpha on the new state
         const double rho = unew[0], ir = 1.0 / rho;  // one FP64 division per cell
@@ -1267,7 +1303,7 @@ constexpr int sweep_min_blocks() {
   return sizeof(R) == 8 ? 1 : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5 : ENOAO_FP32_MIN_BLOCKS_AO7);
 }
 
-template <int NV, int ORDER, typename R>
+template <int NV, int ORDER, typename R, bool DEFER = false>
 __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
     sweep_kernel(const SweepArgs A) {
   constexpr bool FP32 = sizeof(R) == 4;
@@ -1288,13 +1324,19 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
     __syncthreads();
     const long long tile = s_tile;
     if (tile >= A.ntiles) break;
-    sweep_tile<NV, ORDER, R>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax, nfall);
+    sweep_tile<NV, ORDER, R, false, DEFER>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax, nfall);
   }
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1) {
       st->tile_next = 0ull;
       st->blocks_done = 0u;
+      if (DEFER) {
+        // a new tag for the faces this sweep's re-decision pass marks (never 0,
+        // the value of an unmarked face)
+        const unsigned e = st->redo_epoch + 1u;
+        st->redo_epoch = e ? e : 1u;
+      }
       __threadfence();
     }
   }
@@ -1325,6 +1367,309 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
         if (threadIdx.x == 0 && d < A.ndim && v > 0.0)
           atomicMax(&acc[d], (unsigned long long)__double_as_longlong(v));
       }
+    }
+  }
+}
+
+// ------------------------------------------------ grid-wide FP64 re-decisions
+// Near-tie choices cluster at discontinuities and slip lines, in a few tiles
+// whose SMs' FP64 units would then set a sweep's length.  With a list, the
+// sweep instead lists every face that has flagged choices (its owner tile
+// does), uses the FP32 choices throughout, and two passes over the whole grid
+// follow it: redo_kernel re-decides the listed choices in FP64, one face per
+// thread, and applies a change to the face's right cell; redo_apply_kernel
+// then applies it to the face's left cell.  L(u) is linear in the face
+// correction C, so a change dC of face F adds -dC/dx to cell F - 1 and +dC/dx
+// to cell F.  Each cell takes its left face's change first, then its right
+// face's, whatever tiles its faces fell in: the result does not depend on
+// tiles.
+
+// The line and the position along it of face fc (the face layout of the
+// swept axis: nd + 1 faces per line, as tile_geo numbers them).
+__device__ __forceinline__ void face_line(const SweepArgs& A, long long fc, long long& line,
+                                          long long& F, long long& nd, long long& stride_d,
+                                          long long& fstride_d) {
+  const long long n0 = A.n[0], n1 = A.n[1];
+  if (A.dir == 0) {
+    nd = n0; stride_d = 1; fstride_d = 1;
+    const long long li = fc / (n0 + 1);
+    F = fc - li * (n0 + 1);
+    line = li * n0;
+  } else if (A.dir == 1) {
+    nd = n1; stride_d = n0; fstride_d = n0;
+    const long long b = fc / ((n1 + 1) * n0);
+    const long long r = fc - b * (n1 + 1) * n0;
+    F = r / n0;
+    line = b * n1 * n0 + (r - F * n0);
+  } else {
+    nd = A.n[2]; stride_d = n0 * n1; fstride_d = n0 * n1;
+    F = fc / (n0 * n1);
+    line = fc - F * (n0 * n1);
+  }
+}
+
+// Change of face F's correction C (sweep component order) when the choice of
+// field v, sign sgn moves from the FP32 pick to pick64, added into dC: the
+// FP32 window is rebuilt from the state with the arithmetic of phases 1 and
+// 2, and the FP32 pick and value re-derived from it as phase 2b does.
+template <int NV, int ORDER>
+__device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo& g, long long F,
+                                              int v, int sgn, int pick64, double alpha_d,
+                                              float (&dC)[NV], bool& changed) {
+  using GE = Geo<ORDER>;
+  const float gm1 = (float)(A.gamma - 1.0), adv = (float)A.adv_speed;
+  const float halpha = 0.5f * (float)alpha_d;
+  auto cell = [&](long long gi, double (&q)[NV]) {
+    load_state<NV, false>(A.u_in, A.cstride, g.base + bc_map(gi, g.nd, A.bc) * g.stride_d, A.dir, q);
+  };
+  const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+  float L[NV], Rc[NV], w = 0.0f;
+  if constexpr (NV > 1) {
+    double ql64[NV], qr64[NV];
+    cell(F - 1, ql64);
+    cell(F, qr64);
+    float ql[NV], qr[NV], pl[NV], prr[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      ql[c] = f32_rn(ql64[c]);
+      qr[c] = f32_rn(qr64[c]);
+    }
+    roe_prims<NV, float>(ql, gm1, pl);
+    roe_prims<NV, float>(qr, gm1, prr);
+    Eigen<NV, float> E;
+    roe_eigen<NV, float>(pl, prr, gm1, E);
+    left_row<NV, float>(E, v, L);
+    right_col<NV, float>(E, v, Rc);
+    if constexpr (NV >= 4) w = -L[0];
+  } else {
+    L[0] = 1.0f;
+    Rc[0] = 1.0f;
+  }
+  // sign 0: d[i] is f^+ of cells (F-5+i, F-4+i); sign 1: -(f^- of (F+3-i, F+4-i))
+  float d[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = 0.0f;
+#pragma unroll
+  for (int i = GE::LO; i <= GE::HI; ++i) {
+    const long long c0 = sgn == 0 ? F - 5 + i : F + 3 - i;
+    double qa64[NV], qb64[NV];
+    cell(c0, qa64);
+    cell(c0 + 1, qb64);
+    float qa[NV], fp[NV], fm[NV], x[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) qa[c] = f32_rn(qa64[c]);
+    split_diff<NV, float>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) x[c] = sgn == 0 ? fp[c] : fm[c];
+    float acc = 0.0f;
+    if constexpr (NV >= 4) {
+      if (shear) {
+        acc = shear_comp<NV>(x, v) - w * x[0];
+      } else {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc += L[c] * x[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) acc += L[c] * x[c];
+    }
+    d[i] = sgn == 0 ? acc : -acc;
+  }
+  int pick32;
+  bool m;
+  const float nomx[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  const float corr_old = eno_select<ORDER, float, false>(d, (float)A.delta, (float)A.tie_rel, nomx,
+                                                         0.0f, pick32, m);
+  if (pick64 == pick32) return;
+  changed = true;
+  float corr = 0.0f;
+#pragma unroll
+  for (int i = GE::LO; i <= GE::HI; ++i) corr += bcoef<float>(pick64, i) * d[i];
+  const float dv = corr - corr_old;
+  if constexpr (NV >= 4) {
+    if (shear) {  // column v of R is e_v + w e_{NV-1}
+#pragma unroll
+      for (int c = 2; c < NV - 1; ++c) dC[c] += c == v ? dv : 0.0f;
+      dC[NV - 1] += w * dv;
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NV; ++c) dC[c] += Rc[c] * dv;
+}
+
+// Adds s * dC (s = +-1/dx) to L(u) of one cell: to the stored L(u) of a
+// non-final axis, or, on the final axis, to the combined state through the
+// stage's weight of dt L (redo_coef).
+template <int NV>
+__device__ __forceinline__ void apply_change(const SweepArgs& A, long long cell, float s,
+                                             const float (&dC)[NV]) {
+  const bool combine = (A.mode & kModeCombine) != 0;
+  const double w = A.redo_coef * A.st->dt;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    const long long k = perm_comp<NV>(c, A.dir) * A.cstride + cell;
+    const float dL = s * dC[c];
+    if (combine)
+      A.u_out[k] += w * (double)dL;
+    else
+      reinterpret_cast<float*>(A.rhs)[k] += dL;
+  }
+}
+
+// The re-decision pass.  A warp takes CF listed faces at a time and spreads
+// their flagged choices over its lanes, one choice per lane (32 per round):
+// each lane re-decides its choice in FP64 alone (redo_lane), so that one warp
+// instruction of the FP64 unit, whose cost does not shrink with fewer active
+// lanes, serves up to 32 choices; it then re-derives the choice's FP32 pick
+// and value, and each face's lane adds the changes of its choices in field /
+// sign order.  A changed face stores its dC, marks itself with the sweep's
+// epoch and applies the change to its right cell F.
+template <int NV, int ORDER>
+__global__ void __launch_bounds__(128) redo_kernel(const SweepArgs A) {
+  constexpr int CF = 8;  // listed faces per warp round
+  const unsigned FULL = 0xffffffffu;
+  StepState* st = A.st;
+  if (st->skip) return;
+  const unsigned n = st->redo_n < A.redo_cap ? st->redo_n : (unsigned)A.redo_cap;
+  const unsigned epoch = st->redo_epoch;
+  const double alpha_d = st->alpha[A.dir];
+  const float inv_dx = (float)A.inv_dx;
+  const int lane = threadIdx.x & 31;
+  const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+  unsigned long long nf = 0;
+  for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CF; base < n;
+       base += nwarps * CF) {
+    // lane j < CF holds listed face base + j
+    const unsigned i = base + lane;
+    const bool hasf = lane < CF && i < n;
+    const unsigned long long rec = hasf ? A.redo[i] : 0ull;
+    const unsigned mask = (unsigned)(rec & 0xffffull);
+    long long line, F, nd, stride_d, fstride_d;
+    face_line(A, (long long)(rec >> 16), line, F, nd, stride_d, fstride_d);
+    // choices of face j are numbers pre_j .. pre_j + m_j - 1 of the round
+    const int m = __popc(mask);
+    int incl = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int pre = incl - m;
+    const int T = __shfl_sync(FULL, incl, 31);
+    float dC[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) dC[c] = 0.0f;
+    bool changed = false;
+    for (int c0 = 0; c0 < T; c0 += 32) {
+      // lane l takes choice c0 + l: face j, field * 2 + sign k
+      const int ci = c0 + lane;
+      int j = 0;
+#pragma unroll
+      for (int q = 1; q < CF; ++q) {
+        const int pq = __shfl_sync(FULL, pre, q);
+        if (ci >= pq) j = q;
+      }
+      // every lane takes part in each shuffle (none inside a condition)
+      const unsigned mj = __shfl_sync(FULL, mask, j);
+      const int prej = __shfl_sync(FULL, pre, j);
+      const long long lj = __shfl_sync(FULL, line, j), Fj = __shfl_sync(FULL, F, j);
+      const int kb = ci < T ? nth_set_bit(mj, ci - prej) : -1;
+      const bool valid = kb >= 0;
+      const int k = valid ? kb : 0;
+      const int cnt = T - c0 < 32 ? T - c0 : 32;
+      float dk[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) dk[c] = 0.0f;
+      bool ch = false;
+      if (valid) {
+        TileGeo g;  // the face's line, as redo_lane reads it
+        g.base = lj;
+        g.a0 = 0;
+        g.stride_a = 0;
+        g.stride_d = stride_d;
+        g.nd = nd;
+        const int pick64 = redo_lane<NV, ORDER, false>(A, g, 0, Fj - 1, k >> 1, k & 1, alpha_d);
+        face_change32<NV, ORDER>(A, g, Fj, k >> 1, k & 1, pick64, alpha_d, dk, ch);
+        ++nf;
+      }
+      // each face's lane adds its choices' changes in field / sign order
+      for (int l = 0; l < cnt; ++l) {
+        const int jl = __shfl_sync(FULL, j, l);
+        const int chl = __shfl_sync(FULL, (int)ch, l);
+        float v[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) v[c] = __shfl_sync(FULL, dk[c], l);
+        if (lane == jl && chl) {
+#pragma unroll
+          for (int c = 0; c < NV; ++c) dC[c] += v[c];
+          changed = true;
+        }
+      }
+    }
+    if (hasf) {
+      const long long fc = (long long)(rec >> 16);
+      A.redo_mark[fc] = changed ? epoch : 0u;
+      if (changed) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) A.redo_dc[(long long)i * NV + c] = dC[c];
+        if (F < nd) apply_change<NV>(A, line + F * stride_d, inv_dx, dC);
+      }
+    }
+  }
+  if (nf) atomicAdd(&st->fallbacks, nf);
+}
+
+// Second pass: each changed face applies its change to its left cell F - 1.
+// On the final axis the cells a change touched are then checked and enter
+// the next alpha (a cell whose right face also changed is checked by that
+// face's thread, after both of its changes).  The last block to leave empties
+// the list for the next sweep.
+template <int NV>
+__global__ void __launch_bounds__(128) redo_apply_kernel(const SweepArgs A) {
+  StepState* st = A.st;
+  const unsigned n = st->skip ? 0u : (st->redo_n < A.redo_cap ? st->redo_n : (unsigned)A.redo_cap);
+  const unsigned epoch = st->redo_epoch;
+  const float inv_dx = (float)A.inv_dx;
+  const bool check = (A.mode & kModeCombine) != 0;
+  double amax[3] = {0.0, 0.0, 0.0};
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long fc = (long long)(A.redo[i] >> 16);
+    if (A.redo_mark[fc] != epoch) continue;
+    long long line, F, nd, stride_d, fstride_d;
+    face_line(A, fc, line, F, nd, stride_d, fstride_d);
+    float dC[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) dC[c] = A.redo_dc[(long long)i * NV + c];
+    auto check_cell = [&](long long cell) {
+      double u[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) u[c] = A.u_out[c * A.cstride + cell];
+      bulk_state_check<NV>(A, cell, u, A.mode, amax);
+    };
+    if (F >= 1) {
+      apply_change<NV>(A, line + (F - 1) * stride_d, -inv_dx, dC);
+      if (check) check_cell(line + (F - 1) * stride_d);
+    }
+    if (check && F < nd && !(F + 1 <= nd && A.redo_mark[fc + fstride_d] == epoch))
+      check_cell(line + F * stride_d);
+  }
+  if constexpr (NV > 1) {
+    if (check && (A.mode & kModeAlpha)) {
+      unsigned long long* acc = A.stage == 2 ? st->alpha_acc[st->par] : st->alpha_stage;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (d < A.ndim && amax[d] > 0.0)
+          atomicMax(&acc[d], (unsigned long long)__double_as_longlong(amax[d]));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->redo_done, 1u) == gridDim.x - 1) {
+      st->redo_n = 0u;
+      st->redo_done = 0u;
+      __threadfence();
     }
   }
 }

@@ -4,22 +4,36 @@
 
 namespace enoao {
 
+// Two variants per system and order: the sweep that re-decides its near-ties
+// itself, and the one that lists them for the grid-wide pass (a.redo set).
 template <int NV, int ORDER>
 static cudaError_t launch_one(const SweepArgs& a, int grid, int block, size_t smem,
                               cudaStream_t s) {
-  sweep_kernel<NV, ORDER, float><<<grid, block, smem, s>>>(a);
+  if (a.redo)
+    sweep_kernel<NV, ORDER, float, true><<<grid, block, smem, s>>>(a);
+  else
+    sweep_kernel<NV, ORDER, float, false><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int NV, int ORDER>
 static cudaError_t configure_one(size_t smem) {
-  return raise_smem_limit(sweep_kernel<NV, ORDER, float>, smem);
+  cudaError_t e = raise_smem_limit(sweep_kernel<NV, ORDER, float, false>, smem);
+  if (e == cudaSuccess) e = raise_smem_limit(sweep_kernel<NV, ORDER, float, true>, smem);
+  return e;
 }
 
+// The smaller of the two variants' resident blocks per SM.
 template <int NV, int ORDER>
 static cudaError_t occupancy_one(int block, size_t smem, int* per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, sweep_kernel<NV, ORDER, float>,
-                                                       block, smem);
+  int p0 = 0, p1 = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &p0, sweep_kernel<NV, ORDER, float, false>, block, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, sweep_kernel<NV, ORDER, float, true>,
+                                                      block, smem);
+  *per_sm = p0 < p1 ? p0 : p1;
+  return e;
 }
 
 #define ENOAO_DISPATCH(FN, ...)                                 \
@@ -38,6 +52,21 @@ static cudaError_t occupancy_one(int block, size_t smem, int* per_sm) {
 cudaError_t sweep_launch_fp32(int nv, int order, const SweepArgs& a, int grid, int block,
                               size_t smem, cudaStream_t s) {
   ENOAO_DISPATCH(launch_one, a, grid, block, smem, s)
+}
+
+template <int NV, int ORDER>
+static cudaError_t redo_one(const SweepArgs& a, int grid, cudaStream_t s) {
+  redo_kernel<NV, ORDER><<<grid, 128, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  redo_apply_kernel<NV><<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The grid-wide FP64 re-decision pass of a sweep launched with a.redo set (two
+// kernels, stream-ordered after the sweep).
+cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cudaStream_t s) {
+  ENOAO_DISPATCH(redo_one, a, grid, s)
 }
 
 cudaError_t sweep_configure_fp32(int nv, int order, size_t smem) {

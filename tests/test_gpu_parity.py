@@ -242,11 +242,14 @@ TOL32_L1 = 1e-8
 
 
 
+@pytest.mark.parametrize("redecide", [eno.REDECIDE_IN_SWEEP, eno.REDECIDE_GRID])
 @pytest.mark.parametrize("name", ["adv1d-square-ao7", "euler1d-riemann-ao5", "euler1d-riemann-ao7",
                                   "euler2d-quad-ao5", "euler2d-random-ao7", "euler3d-blast-ao7"])
-def test_fp32_bulk_against_oracle(name):
+def test_fp32_bulk_against_oracle(name, redecide):
     s, P, U0 = _make(name, precision=eno.FP32_BULK)
     with s:
+        s.set_redecide(redecide)
+        assert s.uses_grid_redecide() == (redecide == eno.REDECIDE_GRID)
         s.init_state(U0)
         agree = total = 0
         for d in range(len(s.shape)):
@@ -264,16 +267,22 @@ def test_fp32_bulk_against_oracle(name):
 
 
 # ------------------------------------------------- full size, bench launch config
-def test_full_size_2d_workload_sampled_patches():
-    # the 4096^2 benchmark workload, FP64, default tiles after autotune: one
-    # GPU step, then the oracle re-does that step on patches of the same input
-    # (with the full grid's alpha and dt); a patch keeps a 12-cell margin
-    # (three stages x the 4-cell reach of ENO-AO5) that is not compared.
+@pytest.mark.parametrize("precision,redecide", [(eno.FP64, eno.REDECIDE_AUTO),
+                                                (eno.FP32_BULK, eno.REDECIDE_AUTO),
+                                                (eno.FP32_BULK, eno.REDECIDE_GRID)])
+def test_full_size_2d_workload_sampled_patches(precision, redecide):
+    # the 4096^2 benchmark workload, default tiles after autotune (FP32 bulk
+    # also with the grid-wide re-decision pass): one GPU step, then the oracle
+    # re-does that step on patches of the same input (with the full grid's
+    # alpha and dt); a patch keeps a 12-cell margin (three stages x the
+    # 4-cell reach of ENO-AO5) that is not compared.
     import torch
     n = 4096
     U0 = inputs.euler2d_quadrants(n, n, seed=1)
     with eno.Solver((n, n), (0.0, 0.0), (1.0, 1.0), system=eno.EULER, order=5,
-                    bc=eno.TRANSMISSIVE) as s:
+                    bc=eno.TRANSMISSIVE, precision=precision) as s:
+        s.set_redecide(redecide)
+        assert s.uses_grid_redecide() == (redecide == eno.REDECIDE_GRID)
         dev = torch.from_numpy(U0).cuda()
         s.init_state(dev)
         s.autotune()
@@ -299,25 +308,36 @@ def test_full_size_2d_workload_sampled_patches():
         ref = oracle.step_alpha(P, blk, st.dt, np.array(st.alpha[:]))
         r = ref[:, :, y0 - ya:y0 - ya + core, x0 - xa:x0 - xa + core]
         g = got[:, :, y0:y0 + core, x0:x0 + core]
-        assert relerr(g, r) <= TOL64, ((x0, y0), relerr(g, r))
+        if precision == eno.FP64:
+            assert relerr(g, r) <= TOL64, ((x0, y0), relerr(g, r))
+        else:
+            assert relerr(g, r) <= TOL32_STEP, ((x0, y0), relerr(g, r))
+            assert np.abs(g - r).mean() / np.abs(r).mean() <= TOL32_L1, (x0, y0)
 
 
-@pytest.mark.parametrize("precision", [eno.FP64, eno.FP32_BULK])
-def test_results_do_not_depend_on_tiles(precision):
+@pytest.mark.parametrize("precision,redecide", [(eno.FP64, eno.REDECIDE_AUTO),
+                                                (eno.FP32_BULK, eno.REDECIDE_IN_SWEEP),
+                                                (eno.FP32_BULK, eno.REDECIDE_GRID)])
+def test_results_do_not_depend_on_tiles(precision, redecide):
     # every face is a pure function of its window, so tile shapes and the
-    # order in which blocks take tiles must not change a single bit
+    # order in which blocks take tiles must not change a single bit; with the
+    # grid-wide re-decision pass each cell also takes its faces' changes in
+    # one order, whichever tiles they fell in
     n = (130, 75)
     U0 = inputs.euler2d_quadrants(*n, seed=3)
     outs = []
     for tiles in (None, ((1, 31), (16, 7)), ((4, 255), (64, 15)), ((2, 63), (8, 47))):
         with eno.Solver(n, (0.0, 0.0), (1.0, 1.0), system=eno.EULER, order=5,
                         precision=precision) as s:
+            s.set_redecide(redecide)
             if tiles:
                 for d, (ta, ts) in enumerate(tiles):
                     s.set_tiles(d, ta, ts)
             s.init_state(U0)
             s.advance(1e9, cfl=0.5, max_steps=4)
             outs.append(s.get_state())
+            if precision == eno.FP32_BULK:
+                assert s.stats().fp64_fallbacks > 0  # the re-decision path is exercised
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
 
 
@@ -362,9 +382,11 @@ def test_per_stage_alpha_step_matches_oracle(name):
 
 
 @pytest.mark.parametrize("alpha_mode", [eno.ALPHA_PER_STEP, eno.ALPHA_PER_STAGE])
-@pytest.mark.parametrize("precision", [eno.FP64, eno.FP32_BULK])
+@pytest.mark.parametrize("precision,redecide", [(eno.FP64, eno.REDECIDE_AUTO),
+                                                (eno.FP32_BULK, eno.REDECIDE_IN_SWEEP),
+                                                (eno.FP32_BULK, eno.REDECIDE_GRID)])
 @pytest.mark.parametrize("name", ["euler1d-riemann-ao5", "euler2d-random-ao7", "euler3d-blast-ao7"])
-def test_stages_match_oracle_on_their_own_inputs(name, precision, alpha_mode):
+def test_stages_match_oracle_on_their_own_inputs(name, precision, redecide, alpha_mode):
     # Each Runge-Kutta stage against the oracle's spatial operator applied to
     # the stage state this path produced.  A whole FP32-bulk step is not a fair
     # test: stages 2 and 3 start from states that differ from the oracle's by
@@ -379,6 +401,7 @@ def test_stages_match_oracle_on_their_own_inputs(name, precision, alpha_mode):
     per_stage = alpha_mode == eno.ALPHA_PER_STAGE
     with eno.Solver(shape, lo, hi, system=system, order=order, bc=bc, precision=precision,
                     alpha_mode=alpha_mode) as s:
+        s.set_redecide(redecide)
         s.init_state(U)
         G = [U]
         for k in range(3):
@@ -400,3 +423,67 @@ def test_stages_match_oracle_on_their_own_inputs(name, precision, alpha_mode):
             else:
                 assert err <= TOL32_STEP, (k, err)
                 assert np.abs(G[k + 1] - ref).mean() / np.abs(ref).mean() <= TOL32_L1, k
+
+
+# ------------------------------------------------ grid-wide FP64 re-decisions
+def test_redecide_modes_and_defaults():
+    shape = (130, 75)
+    kw = dict(system=eno.EULER, order=5)
+    with eno.Solver(shape, (0.0, 0.0), (1.0, 1.0), precision=eno.FP32_BULK, **kw) as s:
+        assert not s.uses_grid_redecide()  # the default re-decides inside the sweep
+        assert s.launches_per_step() == 1 + 3 * 2
+        s.set_redecide(eno.REDECIDE_GRID)
+        assert s.uses_grid_redecide()
+        assert s.launches_per_step() == 1 + 3 * 2 * 3  # two pass kernels per sweep
+        with pytest.raises(eno.EnoaoError):
+            s.set_redecide(7)
+    with eno.Solver((1024, 512), (0.0, 0.0), (1.0, 1.0), precision=eno.FP32_BULK, **kw) as s:
+        assert not s.uses_grid_redecide()  # the default at any size
+        s.set_redecide(eno.REDECIDE_GRID)
+        assert s.uses_grid_redecide()
+        s.set_redecide(eno.REDECIDE_IN_SWEEP)
+        assert not s.uses_grid_redecide()
+    with eno.Solver((1024, 512), (0.0, 0.0), (1.0, 1.0), precision=eno.FP64, **kw) as s:
+        s.set_redecide(eno.REDECIDE_GRID)
+        assert not s.uses_grid_redecide()  # FP64 has nothing to re-decide
+
+
+@pytest.mark.parametrize("order", [5, 7])
+def test_grid_redecide_on_riemann_slip_lines(order):
+    # 2D Riemann configuration 2 evolved until its slip lines carry many
+    # near-ties; then each Runge-Kutta stage in each re-decision mode against
+    # the oracle's operator on the stage input this path produced (as in
+    # test_stages_match_oracle_on_their_own_inputs), and the first stage of
+    # the two modes, which starts from the same state, against each other
+    n = 160
+    U = inputs.riemann2d(2, n, n)
+    kw = dict(system=eno.EULER, order=order, bc=eno.TRANSMISSIVE)
+    with eno.Solver((n, n), (-1.0, -1.0), (1.0, 1.0), **kw) as s:
+        s.init_state(U)
+        s.advance(1e9, cfl=0.5, max_steps=60)
+        U = s.get_state()
+    P = oracle.make_problem((n, n), (-1.0, -1.0), (1.0, 1.0), **kw)
+    a0 = np.asarray(oracle.alpha(P, U))
+    dt = 0.5 / sum(a0[d] * n / 2.0 for d in range(2))
+    first = {}
+    for mode in (eno.REDECIDE_IN_SWEEP, eno.REDECIDE_GRID):
+        with eno.Solver((n, n), (-1.0, -1.0), (1.0, 1.0), precision=eno.FP32_BULK, **kw) as s:
+            s.set_redecide(mode)
+            s.init_state(U)
+            G = [U]
+            for k in range(3):
+                s.rk_stage(k, dt)
+                G.append(s.get_stage_state(k + 1) if k < 2 else s.get_state())
+                Lk = oracle.rhs(P, G[k], a0)
+                if k == 0:
+                    ref = U + dt * Lk
+                elif k == 1:
+                    ref = 0.75 * U + 0.25 * (G[1] + dt * Lk)
+                else:
+                    ref = U / 3.0 + 2.0 / 3.0 * (G[2] + dt * Lk)
+                err = relerr(G[k + 1], ref)
+                assert err <= TOL32_STEP, (mode, k, err)
+                assert np.abs(G[k + 1] - ref).mean() / np.abs(ref).mean() <= TOL32_L1, (mode, k)
+            assert s.stats().fp64_fallbacks > 100, s.stats().fp64_fallbacks
+            first[mode] = G[1]
+    assert relerr(first[eno.REDECIDE_GRID], first[eno.REDECIDE_IN_SWEEP]) <= TOL32_STEP
