@@ -505,7 +505,8 @@ def run_small(args, workload):
 
 def run_paper_cases(args):
     """The paper's printed test cases (Sec. 4) at its resolutions and end times,
-    FP32 bulk and FP64: composite advection wave (dx = 1/200 on [-1, 1], t = 20),
+    FP32 bulk and FP64 (the 2D cases also FP32 bulk with the grid-wide FP64
+    re-decision pass): composite advection wave (dx = 1/200 on [-1, 1], t = 20),
     Lax tube (dx = 1/100 on [0, 2], t = 0.26), Titarev-Toro (dx = 1/200 on
     [-5, 5], t = 5), 2D Riemann configurations 1 and 2 (800 x 800 cells on
     [-1, 1]^2, t = 1); ENO-AO5 and ENO-AO7.  Whole runs timed on the host clock
@@ -531,9 +532,13 @@ def run_paper_cases(args):
         cells = int(np.prod(shape))
         for order in (5, 7):
             res = {}
-            for pname, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
+            variants = [("fp32_bulk", eno.FP32_BULK, eno.REDECIDE_AUTO), ("fp64", eno.FP64, eno.REDECIDE_AUTO)]
+            if len(shape) > 1:  # shock / slip-line flows: also the grid-wide re-decision pass
+                variants.append(("fp32_bulk_grid", eno.FP32_BULK, eno.REDECIDE_GRID))
+            for pname, prec, redecide in variants:
                 with eno.Solver(shape, lo, hi, system=system, order=order, bc=bc,
                                 precision=prec) as s:
+                    s.set_redecide(redecide)
                     s.init_state(U)
                     s.advance_steps(1, CFL)     # graph capture outside the timed run
                     s.init_state(U)
@@ -549,6 +554,11 @@ def run_paper_cases(args):
                    "fp64_cell_stage_per_s": cells * 3 * res["fp64"][1] / res["fp64"][2],
                    "fp32_bulk_seconds": res["fp32_bulk"][2], "fp64_seconds": res["fp64"][2],
                    "l1_rel_fp32_bulk_vs_fp64": float(np.abs(a - b).mean() / np.abs(b).mean())}
+            if "fp32_bulk_grid" in res:
+                g = res["fp32_bulk_grid"]
+                row["fp32_bulk_grid_cell_stage_per_s"] = cells * 3 * g[1] / g[2]
+                row["fp32_bulk_grid_seconds"] = g[2]
+                row["l1_rel_fp32_bulk_grid_vs_fp64"] = float(np.abs(g[0] - b).mean() / np.abs(b).mean())
             if bc == eno.PERIODIC:
                 row["conservation_rel_fp64"] = float(abs(b.sum() - U.sum()) / np.abs(U).sum())
             if system == eno.EULER:

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
     A.n[0] = n;
     A.n[1] = A.n[2] = 1;
     A.ncell = n;
+    A.nfaces = n + 1;
     A.cstride = B.total;
     A.ndim = 1;
     A.dir = 0;

@@ -320,6 +320,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.ts = c->ts[d];
   a.se = sweep_row_pitch(c->nv, c->cfg.order, fp32(c), d, a.ta, a.ts);
   const long long nd = c->cfg.n[d];
+  a.nfaces = c->ncell / nd * (nd + 1);
   a.tiles_s = (nd + a.ts - 1) / a.ts;
   if (d == 0) {
     const long long rows = c->cfg.n[1] * c->cfg.n[2];

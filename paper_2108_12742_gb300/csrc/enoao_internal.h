@@ -70,6 +70,7 @@ struct SweepArgs {
   StepState* st;
   long long n[3];       // cells per axis
   long long ncell;      // total cells
+  long long nfaces;     // faces of the swept axis, ncell / nd * (nd + 1) (flux output layout)
   long long cstride;    // distance between two conserved components in the state arrays
   int ndim;
   int dir;              // swept axis

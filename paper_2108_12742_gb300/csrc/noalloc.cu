@@ -156,6 +156,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   a.n[0] = n;
   a.n[1] = a.n[2] = 1;
   a.ncell = n;
+  a.nfaces = n + 1;
   a.cstride = n;  // U1/U2 use the caller's layout [nv][n]
   a.ndim = 1;
   a.dir = 0;

@@ -988,7 +988,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
             if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 (phase 2b or the pass)
           }
           if ((mode & kModeFlux) && A.idx_out && own) {
-            const long long nf = A.ncell / g.nd * (g.nd + 1);
+            const long long nf = A.nfaces;
             const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
             A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
           }
@@ -1060,7 +1060,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       e0 = tid >> lgTA;
       estep = bd >> lgTA;
     }
-    const int rounds = (cnt + estep - 1) / estep;  // the same for every lane
+    // estep is a power of two (blocks of 128 threads): no integer division,
+    // which runs partly on the FP64 unit
+    const int rounds = (cnt + estep - 1) >> (__ffs(estep) - 1);  // the same for every lane
     for (int rd = 0; rd < rounds; ++rd) {
       const int f = e0 + rd * estep;
       const bool valid = f < cnt && g.a0 + al < g.na;
@@ -1171,7 +1173,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           }
         }
         if ((mode & kModeFlux) && A.idx_out && own) {
-          const long long nf = A.ncell / g.nd * (g.nd + 1);
+          const long long nf = A.nfaces;
           const long long fc = g.fbase + (g.a0 + al) * g.fstride_a + gface * g.fstride_d;
           A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
         }
@@ -1189,7 +1191,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // ---------------- phase 3: flux difference and Runge-Kutta combine
   if (mode & kModeFlux) {
     const int cnt = nts + 1;
-    const long long nf = A.ncell / g.nd * (g.nd + 1);
+    const long long nf = A.nfaces;
     for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
       if (g.a0 + a >= g.na) return;
       const long long gface = g.s0 + f;
