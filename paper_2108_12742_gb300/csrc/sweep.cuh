@@ -199,67 +199,78 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
       }
   }
   if constexpr (CHECK) {
-    // per-candidate bounds: Pascal sums of e over each indicator's differences
-    R q2[8], q3[8], q4[8], q5[8], q6[8], q7[8];
-#pragma unroll
-    for (int i = LO; i < HI; ++i) q2[i] = e[i] + e[i + 1];
-#pragma unroll
-    for (int i = LO; i < HI - 1; ++i) q3[i] = q2[i] + q2[i + 1];
-#pragma unroll
-    for (int i = LO; i < HI - 2; ++i) q4[i] = q3[i] + q3[i + 1];
-#pragma unroll
-    for (int i = LO; i < HI - 3; ++i) q5[i] = q4[i] + q4[i + 1];
-    R tol[9];
-    tol[0] = feps * R(0.5) * fmaxf(e[3] + e[2], e[4] + e[5]);
-    tol[1] = feps * fmaxf(q2[3], q2[4]);
-    tol[2] = feps * fmaxf(q3[2], q3[3]);
-    tol[3] = feps * fmaxf(q4[1], q4[2]);
-    tol[4] = feps * fmaxf(q4[2], q4[3]);
-    tol[5] = feps * fmaxf(q5[1], q5[2]);
-    if constexpr (ORDER == 7) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) q6[i] = q5[i] + q5[i + 1];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) q7[i] = q6[i] + q6[i + 1];
-      tol[6] = feps * fmaxf(q6[0], q6[1]);
-      tol[7] = feps * fmaxf(q6[1], q6[2]);
-      tol[8] = feps * fmaxf(q7[0], q7[1]);
-    }
     const R rel = tie_rel * delta;
     bool m = false;
     if (thr && pick == NC - 1) {
-      // top candidate below the threshold (smooth data): only it decides
-      m = rabs(IS[NC - 1] - delta) <= rel + tol[NC - 1];
-    } else if (thr) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= rel + tol[c]);
-    } else {
-      R tp = tol[0];
-#pragma unroll
-      for (int c = 1; c < NC; ++c)
-        if (c == pick) tp = tol[c];
-      m = (best - delta) <= rel + tp;
-      const R relA = tie_rel * best + tp;
-      // Candidates 3 and 4 (and 6 and 7 of ENO-AO7) take the minimum over
-      // two differences of which they share the middle one, b: with
-      // IS_lo = min(a, b) and IS_hi = min(b, c), IS_lo wins exactly when
-      // a < b and a < c, so the margin of the pair is max(a - b, a - c), not
-      // IS_lo - IS_hi (which is zero whenever b is the smaller of both).
-      R gap[9];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) gap[c] = IS[c] - best;
-      if (pick == 4) {
-        const R a = rabs(s4[1]), b = rabs(s4[2]), c = rabs(s4[3]);
-        gap[3] = fmaxf(a - b, a - c);
-      }
+      // top candidate below the threshold (smooth data): only it decides, and
+      // only its bound is formed (the Pascal sums below, written out)
+      R qa, qb;
       if constexpr (ORDER == 7) {
-        if (pick == 7) {
-          const R a = rabs(s6[0]), b = rabs(s6[1]), c = rabs(s6[2]);
-          gap[6] = fmaxf(a - b, a - c);
-        }
+        qa = e[0] + e[6] + R(6) * (e[1] + e[5]) + R(15) * (e[2] + e[4]) + R(20) * e[3];
+        qb = e[1] + e[7] + R(6) * (e[2] + e[6]) + R(15) * (e[3] + e[5]) + R(20) * e[4];
+      } else {
+        qa = e[1] + e[5] + R(4) * (e[2] + e[4]) + R(6) * e[3];
+        qb = e[2] + e[6] + R(4) * (e[3] + e[5]) + R(6) * e[4];
       }
+      m = rabs(IS[NC - 1] - delta) <= rel + feps * fmaxf(qa, qb);
+    } else {
+      // per-candidate bounds: Pascal sums of e over each indicator's differences
+      R q2[8], q3[8], q4[8], q5[8], q6[8], q7[8];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) m |= (c != pick) && (gap[c] <= relA + tol[c]);
+      for (int i = LO; i < HI; ++i) q2[i] = e[i] + e[i + 1];
+#pragma unroll
+      for (int i = LO; i < HI - 1; ++i) q3[i] = q2[i] + q2[i + 1];
+#pragma unroll
+      for (int i = LO; i < HI - 2; ++i) q4[i] = q3[i] + q3[i + 1];
+#pragma unroll
+      for (int i = LO; i < HI - 3; ++i) q5[i] = q4[i] + q4[i + 1];
+      R tol[9];
+      tol[0] = feps * R(0.5) * fmaxf(e[3] + e[2], e[4] + e[5]);
+      tol[1] = feps * fmaxf(q2[3], q2[4]);
+      tol[2] = feps * fmaxf(q3[2], q3[3]);
+      tol[3] = feps * fmaxf(q4[1], q4[2]);
+      tol[4] = feps * fmaxf(q4[2], q4[3]);
+      tol[5] = feps * fmaxf(q5[1], q5[2]);
+      if constexpr (ORDER == 7) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) q6[i] = q5[i] + q5[i + 1];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) q7[i] = q6[i] + q6[i + 1];
+        tol[6] = feps * fmaxf(q6[0], q6[1]);
+        tol[7] = feps * fmaxf(q6[1], q6[2]);
+        tol[8] = feps * fmaxf(q7[0], q7[1]);
+      }
+      if (thr) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) m |= (c >= pick) && (rabs(IS[c] - delta) <= rel + tol[c]);
+      } else {
+        R tp = tol[0];
+#pragma unroll
+        for (int c = 1; c < NC; ++c)
+          if (c == pick) tp = tol[c];
+        m = (best - delta) <= rel + tp;
+        const R relA = tie_rel * best + tp;
+        // Candidates 3 and 4 (and 6 and 7 of ENO-AO7) take the minimum over
+        // two differences of which they share the middle one, b: with
+        // IS_lo = min(a, b) and IS_hi = min(b, c), IS_lo wins exactly when
+        // a < b and a < c, so the margin of the pair is max(a - b, a - c), not
+        // IS_lo - IS_hi (which is zero whenever b is the smaller of both).
+        R gap[9];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) gap[c] = IS[c] - best;
+        if (pick == 4) {
+          const R a = rabs(s4[1]), b = rabs(s4[2]), c = rabs(s4[3]);
+          gap[3] = fmaxf(a - b, a - c);
+        }
+        if constexpr (ORDER == 7) {
+          if (pick == 7) {
+            const R a = rabs(s6[0]), b = rabs(s6[1]), c = rabs(s6[2]);
+            gap[6] = fmaxf(a - b, a - c);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) m |= (c != pick) && (gap[c] <= relA + tol[c]);
+      }
     }
     marginal = m;
   }
