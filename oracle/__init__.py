@@ -49,6 +49,7 @@ class Problem(ctypes.Structure):
         ("ndim", ctypes.c_int), ("system", ctypes.c_int), ("order", ctypes.c_int),
         ("nthreads", ctypes.c_int), ("n", ctypes.c_long * 3),
         ("dx", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("alpha_per_stage", ctypes.c_int),
+        ("alpha_per_field", ctypes.c_int),
         ("adv_speed", ctypes.c_double), ("gamma", ctypes.c_double),
         ("delta", ctypes.c_double),
     ]
@@ -70,6 +71,11 @@ def _load():
             lib.or_euler_eigen.argtypes = [ctypes.c_int, ctypes.c_double, D,
                                            ctypes.c_double, D, D]
             lib.or_alpha.argtypes = [P, D, D]
+            lib.or_alpha_fields.argtypes = [P, D, D]
+            lib.or_fluxes_fields.argtypes = [P, D, ctypes.c_int, D, D,
+                                             ctypes.POINTER(ctypes.c_byte), D]
+            lib.or_rhs_fields.argtypes = [P, D, D, D]
+            lib.or_step_alpha_fields.argtypes = [P, D, ctypes.c_double, D]
             lib.or_fluxes.argtypes = [P, D, ctypes.c_int, D, D,
                                       ctypes.POINTER(ctypes.c_byte), D]
             lib.or_rhs.argtypes = [P, D, D, D]
@@ -88,9 +94,12 @@ def _dp(a):
 
 def make_problem(shape, lo, hi, system=EULER, order=5, bc=TRANSMISSIVE,
                  adv_speed=1.0, gamma=1.4, delta=1e-5, nthreads=0,
-                 alpha_per_stage=False) -> Problem:
+                 alpha_per_stage=False, alpha_per_field=False) -> Problem:
     """shape = (nx,) / (nx, ny) / (nx, ny, nz); lo/hi per axis; bc scalar or per axis;
-    alpha_per_stage: each Runge-Kutta stage splits with the alpha of its own input state."""
+    alpha_per_stage: each Runge-Kutta stage splits with the alpha of its own input state;
+    alpha_per_field: each characteristic field k splits with max |lambda_k| (Euler).
+    With alpha_per_field the alpha arguments below are the (3, 5) per-field arrays
+    of ``alpha_fields``."""
     ndim = len(shape)
     P = Problem()
     P.ndim, P.system, P.order, P.nthreads = ndim, system, order, nthreads
@@ -104,6 +113,7 @@ def make_problem(shape, lo, hi, system=EULER, order=5, bc=TRANSMISSIVE,
             P.n[d], P.dx[d], P.bc[d] = 1, 1.0, PERIODIC
     P.adv_speed, P.gamma, P.delta = adv_speed, gamma, delta
     P.alpha_per_stage = int(bool(alpha_per_stage))
+    P.alpha_per_field = int(bool(alpha_per_field))
     return P
 
 
@@ -167,6 +177,27 @@ def alpha(P, U):
     return a
 
 
+def alpha_fields(P, U):
+    """Per-field splitting constants, shape (3, 5): [d, k] = max |lambda_k| along d."""
+    U = _state(P, U)
+    a = np.zeros(15)
+    st = _load().or_alpha_fields(ctypes.byref(P), _dp(U), _dp(a))
+    if st:
+        raise FloatingPointError("oracle: non-physical state")
+    return a.reshape(3, 5)
+
+
+def _per_field(P):
+    return bool(P.alpha_per_field) and P.system == EULER
+
+
+def _alpha_arg(P, U, alpha_vec):
+    if _per_field(P):
+        a = alpha_fields(P, U) if alpha_vec is None else alpha_vec
+        return np.ascontiguousarray(a, dtype=np.float64).reshape(15)
+    return alpha(P, U) if alpha_vec is None else np.ascontiguousarray(alpha_vec, dtype=np.float64)
+
+
 def face_shape(P, d):
     nv = nvars(P)
     n = [P.n[0], P.n[1], P.n[2]]
@@ -177,12 +208,13 @@ def face_shape(P, d):
 def fluxes(P, U, d, alpha_vec=None, want_idx=False):
     """Interface fluxes along axis d: (Fhat, idx, gap) with face-major layout."""
     U = _state(P, U)
-    a = alpha(P, U) if alpha_vec is None else np.ascontiguousarray(alpha_vec, dtype=np.float64)
+    a = _alpha_arg(P, U, alpha_vec)
     shp = face_shape(P, d)
     F = np.zeros(shp)
     idx = np.zeros((shp[0], 2) + shp[1:], dtype=np.int8) if want_idx else None
     gap = np.zeros((shp[0], 2) + shp[1:]) if want_idx else None
-    st = _load().or_fluxes(ctypes.byref(P), _dp(U), d, _dp(a), _dp(F),
+    fn = _load().or_fluxes_fields if _per_field(P) else _load().or_fluxes
+    st = fn(ctypes.byref(P), _dp(U), d, _dp(a), _dp(F),
                            idx.ctypes.data_as(ctypes.POINTER(ctypes.c_byte)) if want_idx else None,
                            _dp(gap) if want_idx else None)
     assert st == 0
@@ -191,9 +223,10 @@ def fluxes(P, U, d, alpha_vec=None, want_idx=False):
 
 def rhs(P, U, alpha_vec=None):
     U = _state(P, U)
-    a = alpha(P, U) if alpha_vec is None else np.ascontiguousarray(alpha_vec, dtype=np.float64)
+    a = _alpha_arg(P, U, alpha_vec)
     out = np.zeros_like(U)
-    _load().or_rhs(ctypes.byref(P), _dp(U), _dp(a), _dp(out))
+    fn = _load().or_rhs_fields if _per_field(P) else _load().or_rhs
+    fn(ctypes.byref(P), _dp(U), _dp(a), _dp(out))
     return out
 
 
@@ -208,8 +241,9 @@ def step(P, U, dt):
 def step_alpha(P, U, dt, alpha_vec):
     """One step with the splitting constants of the full mesh given."""
     U = _state(P, U).copy()
-    a = np.ascontiguousarray(alpha_vec, dtype=np.float64)
-    _load().or_step_alpha(ctypes.byref(P), _dp(U), dt, _dp(a))
+    a = _alpha_arg(P, U, alpha_vec)
+    fn = _load().or_step_alpha_fields if _per_field(P) else _load().or_step_alpha
+    fn(ctypes.byref(P), _dp(U), dt, _dp(a))
     return U
 
 

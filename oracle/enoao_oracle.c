@@ -259,8 +259,9 @@ static long bc_map(long i, long n, int bc) {
  * ghost cells on each side, (n + 2*GHOST) x nv, momentum permuted so that
  * component 1 is the one along d.  Writes (n+1) x nv interface fluxes. */
 static void line_fluxes(const or_problem *P, int nv, long n, const double *q,
-                        double alpha, double *Fh, signed char *idx_line,
-                        double *gap_line, long idx_stride, double *work) {
+                        double alpha, const double *alpha_v, double *Fh,
+                        signed char *idx_line, double *gap_line, long idx_stride,
+                        double *work) {
   const int order = P->order;
   const int reach = order / 2 + 2; /* cells j-reach+1 .. j+reach used by face j+1/2 */
   double *fp = work;               /* split fluxes of the window, [2*reach][nv] */
@@ -271,13 +272,20 @@ static void line_fluxes(const or_problem *P, int nv, long n, const double *q,
 
   for (long f = 0; f <= n; ++f) {
     long j = f - 1; /* face j+1/2 */
-    /* split fluxes f^+- = (F +- alpha q)/2 of the window cells */
+    /* split fluxes f^+- = (F +- alpha q)/2 of the window cells; with
+     * per-field constants, fp and fm hold F and q themselves and the split
+     * follows the projection (alpha differs per field) */
     for (int s = 0; s < 2 * reach; ++s) {
       const double *qk = q + (j - reach + 1 + s + GHOST) * nv;
       phys_flux(P, qk, nv, Fk);
       for (int v = 0; v < nv; ++v) {
-        fp[s * nv + v] = 0.5 * (Fk[v] + alpha * qk[v]);
-        fm[s * nv + v] = 0.5 * (Fk[v] - alpha * qk[v]);
+        if (alpha_v) {
+          fp[s * nv + v] = Fk[v];
+          fm[s * nv + v] = qk[v];
+        } else {
+          fp[s * nv + v] = 0.5 * (Fk[v] + alpha * qk[v]);
+          fm[s * nv + v] = 0.5 * (Fk[v] - alpha * qk[v]);
+        }
       }
     }
     int euler = P->system == OR_EULER;
@@ -300,8 +308,13 @@ static void line_fluxes(const or_problem *P, int nv, long n, const double *q,
           a = fp[s * nv + v];
           b = fm[s * nv + v];
         }
-        wp[s] = a;
-        wm[s] = b;
+        if (alpha_v) { /* a = L_v F, b = L_v q */
+          wp[s] = 0.5 * (a + alpha_v[v] * b);
+          wm[s] = 0.5 * (a - alpha_v[v] * b);
+        } else {
+          wp[s] = a;
+          wm[s] = b;
+        }
       }
       /* f^+ : window centred on cell j, wp[s] is cell j-reach+1+s */
       double win[9], gp, gm;
@@ -393,8 +406,9 @@ static void load_line(const or_problem *P, const double *U, int d, long l,
   }
 }
 
-int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
-              double *Fhat, signed char *idx, double *gap) {
+/* alpha: one constant per axis, or (alpha_f non-null) per axis and field */
+static int fluxes_impl(const or_problem *P, const double *U, int d, const double *alpha,
+                       const double *alpha_f, double *Fhat, signed char *idx, double *gap) {
   if (d < 0 || d >= P->ndim) return 1;
   int nv = or_nvars(P);
   long n = P->n[d], nlines = n_cells(P) / n;
@@ -410,7 +424,8 @@ int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
 #pragma omp for schedule(static)
     for (long l = 0; l < nlines; ++l) {
       load_line(P, U, d, l, nv, q);
-      line_fluxes(P, nv, n, q, alpha[d], Fh, il, gl, n + 1, work);
+      line_fluxes(P, nv, n, q, alpha_f ? 0.0 : alpha[d], alpha_f ? alpha_f + 5 * d : NULL, Fh,
+                  il, gl, n + 1, work);
       for (long f = 0; f <= n; ++f) {
         long fi = line_face(P, d, l, f);
         for (int c = 0; c < nv; ++c) {
@@ -434,7 +449,18 @@ int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
   return 0;
 }
 
-int or_rhs(const or_problem *P, const double *U, const double *alpha, double *rhs) {
+int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
+              double *Fhat, signed char *idx, double *gap) {
+  return fluxes_impl(P, U, d, alpha, NULL, Fhat, idx, gap);
+}
+
+int or_fluxes_fields(const or_problem *P, const double *U, int d, const double *alpha_f,
+                     double *Fhat, signed char *idx, double *gap) {
+  return fluxes_impl(P, U, d, NULL, alpha_f, Fhat, idx, gap);
+}
+
+static int rhs_impl(const or_problem *P, const double *U, const double *alpha,
+                    const double *alpha_f, double *rhs) {
   int nv = or_nvars(P);
   long N = n_cells(P);
   memset(rhs, 0, sizeof(double) * nv * N);
@@ -450,7 +476,8 @@ int or_rhs(const or_problem *P, const double *U, const double *alpha, double *rh
 #pragma omp for schedule(static)
       for (long l = 0; l < nlines; ++l) {
         load_line(P, U, d, l, nv, q);
-        line_fluxes(P, nv, n, q, alpha[d], Fh, NULL, NULL, n + 1, work);
+        line_fluxes(P, nv, n, q, alpha_f ? 0.0 : alpha[d], alpha_f ? alpha_f + 5 * d : NULL, Fh,
+                    NULL, NULL, n + 1, work);
         for (long s = 0; s < n; ++s) {
           long cell = line_cell(P, d, l, s);
           for (int c = 0; c < nv; ++c) {
@@ -462,6 +489,40 @@ int or_rhs(const or_problem *P, const double *U, const double *alpha, double *rh
       }
       free(q);
       free(Fh);
+    }
+  }
+  return 0;
+}
+
+int or_rhs(const or_problem *P, const double *U, const double *alpha, double *rhs) {
+  return rhs_impl(P, U, alpha, NULL, rhs);
+}
+
+int or_rhs_fields(const or_problem *P, const double *U, const double *alpha_f, double *rhs) {
+  return rhs_impl(P, U, NULL, alpha_f, rhs);
+}
+
+int or_alpha_fields(const or_problem *P, const double *U, double *alpha_f) {
+  long N = n_cells(P);
+  int nv = or_nvars(P);
+  for (int i = 0; i < 15; ++i) alpha_f[i] = 0.0;
+  if (P->system == OR_SCALAR) {
+    for (int d = 0; d < P->ndim; ++d) alpha_f[5 * d] = fabs(P->adv_speed);
+    return 0;
+  }
+  for (long c = 0; c < N; ++c) {
+    double q[5];
+    for (int v = 0; v < nv; ++v) q[v] = U[v * N + c];
+    double p = euler_pressure(q, nv, P->gamma);
+    if (!(q[0] > 0.0) || !(p > 0.0)) return 2; /* non-physical state */
+    double a = sqrt(P->gamma * p / q[0]);
+    for (int d = 0; d < P->ndim; ++d) {
+      double u = q[1 + d] / q[0];
+      /* eigenvalues of the flux Jacobian along d, fields (u-c, entropy, shear..., u+c) */
+      for (int k = 0; k < nv; ++k) {
+        double lam = k == 0 ? u - a : (k == nv - 1 ? u + a : u);
+        if (fabs(lam) > alpha_f[5 * d + k]) alpha_f[5 * d + k] = fabs(lam);
+      }
     }
   }
   return 0;
@@ -490,47 +551,58 @@ int or_alpha(const or_problem *P, const double *U, double *alpha) {
 }
 
 /* The three stages of the third-order TVD Runge-Kutta scheme (Sec. 2).
- * Stage 0 splits with alpha0; with per_stage set, stages 1 and 2 split with
- * the alpha of their own input state (u1, u2) instead. */
+ * Stage 0 splits with alpha0 (3 values, or 15 per field with per_field);
+ * with per_stage set, stages 1 and 2 split with the alpha of their own input
+ * state (u1, u2) instead. */
 static int rk3_step(const or_problem *P, double *U, double dt, const double *alpha0,
-                    int per_stage) {
+                    int per_stage, int per_field) {
   int nv = or_nvars(P);
   long M = (long)nv * n_cells(P);
   double *u0 = malloc(sizeof(double) * M);
   double *L = malloc(sizeof(double) * M);
-  double alpha[3] = {alpha0[0], alpha0[1], alpha0[2]};
+  double alpha[15];
+  for (int i = 0; i < (per_field ? 15 : 3); ++i) alpha[i] = alpha0[i];
   int st = 0;
+#define OR_STAGE_ALPHA() (per_field ? or_alpha_fields(P, U, alpha) : or_alpha(P, U, alpha))
+#define OR_STAGE_RHS() (per_field ? or_rhs_fields(P, U, alpha, L) : or_rhs(P, U, alpha, L))
   memcpy(u0, U, sizeof(double) * M);
   /* u1 = u0 + dt L(u0) */
-  or_rhs(P, U, alpha, L);
+  OR_STAGE_RHS();
   for (long i = 0; i < M; ++i) U[i] = u0[i] + dt * L[i];
   /* u2 = 3/4 u0 + 1/4 (u1 + dt L(u1)) */
-  if (per_stage) st = or_alpha(P, U, alpha);
+  if (per_stage) st = OR_STAGE_ALPHA();
   if (!st) {
-    or_rhs(P, U, alpha, L);
+    OR_STAGE_RHS();
     for (long i = 0; i < M; ++i) U[i] = 0.75 * u0[i] + 0.25 * (U[i] + dt * L[i]);
     /* u^{n+1} = 1/3 u0 + 2/3 (u2 + dt L(u2)) */
-    if (per_stage) st = or_alpha(P, U, alpha);
+    if (per_stage) st = OR_STAGE_ALPHA();
   }
   if (!st) {
-    or_rhs(P, U, alpha, L);
+    OR_STAGE_RHS();
     for (long i = 0; i < M; ++i)
       U[i] = (1.0 / 3.0) * u0[i] + (2.0 / 3.0) * (U[i] + dt * L[i]);
   }
+#undef OR_STAGE_ALPHA
+#undef OR_STAGE_RHS
   free(u0);
   free(L);
   return st;
 }
 
 int or_step(const or_problem *P, double *U, double dt) {
-  double alpha[3];
-  int st = or_alpha(P, U, alpha);
+  const int euler = P->system == OR_EULER;
+  double alpha[15];
+  int st = P->alpha_per_field && euler ? or_alpha_fields(P, U, alpha) : or_alpha(P, U, alpha);
   if (st) return st;
-  return rk3_step(P, U, dt, alpha, P->alpha_per_stage && P->system == OR_EULER);
+  return rk3_step(P, U, dt, alpha, P->alpha_per_stage && euler, P->alpha_per_field && euler);
 }
 
 int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha) {
-  return rk3_step(P, U, dt, alpha, 0);
+  return rk3_step(P, U, dt, alpha, 0, 0);
+}
+
+int or_step_alpha_fields(const or_problem *P, double *U, double dt, const double *alpha_f) {
+  return rk3_step(P, U, dt, alpha_f, 0, 1);
 }
 
 int or_advance(const or_problem *P, double *U, double t_end, double cfl,

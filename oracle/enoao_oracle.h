@@ -33,6 +33,11 @@ typedef struct {
   int bc[3];         /* OR_PERIODIC or OR_TRANSMISSIVE per axis */
   int alpha_per_stage; /* 0: alpha of U^n for all three stages; 1: each stage
                           takes alpha of its own input state (dt from U^n) */
+  int alpha_per_field; /* 0: one alpha per axis for every characteristic field;
+                          1 (Euler): field k splits with alpha_k = max over the
+                          mesh of |lambda_k| (u_d - c, u_d, ..., u_d + c), the
+                          component-wise Lax-Friedrichs reading of Eq.
+                          (LF_Flux_Split) applied in characteristic variables */
   double adv_speed;  /* a in f(u) = a*u (scalar only) */
   double gamma;      /* ratio of specific heats (Euler only) */
   double delta;      /* selection threshold of Sec. 3.2 (1e-5 in the paper) */
@@ -65,6 +70,12 @@ void or_euler_eigen(int ndim, double gamma, const double *vel, double H,
 /* Lax-Friedrichs alpha per axis (max over the mesh of |df/du|). */
 int or_alpha(const or_problem *P, const double *U, double *alpha);
 
+/* Per-field splitting constants: alpha_f[d*5 + k] = max over the mesh of
+ * |lambda_k| along axis d, with lambda = (u_d - c, u_d, ..., u_d, u_d + c) for
+ * the Euler fields (u-c, entropy, shear..., u+c); |a| for scalar advection.
+ * Entries beyond ndim / nv are zero. */
+int or_alpha_fields(const or_problem *P, const double *U, double *alpha_f);
+
 /* Interface fluxes along axis d for state U with splitting constants alpha.
  * Fhat has the layout of U with n[d] replaced by n[d]+1 faces; face f sits
  * between cells f-1 and f.  idx (nullable) holds, per characteristic field
@@ -78,9 +89,18 @@ int or_fluxes(const or_problem *P, const double *U, int d, const double *alpha,
 int or_rhs(const or_problem *P, const double *U, const double *alpha,
            double *rhs);
 
+/* or_fluxes and or_rhs with per-field splitting constants alpha_f (layout of
+ * or_alpha_fields): the window's physical fluxes and states are projected
+ * separately and field k splits as w^+- = (L_k f +- alpha_k L_k u) / 2. */
+int or_fluxes_fields(const or_problem *P, const double *U, int d, const double *alpha_f,
+                     double *Fhat, signed char *idx, double *gap);
+int or_rhs_fields(const or_problem *P, const double *U, const double *alpha_f,
+                  double *rhs);
+
 /* One third-order TVD Runge-Kutta step of size dt, alpha taken from U at the
  * start of the step (and, with alpha_per_stage, from each later stage's
- * input state for that stage).  U is updated in place. */
+ * input state for that stage); per field with alpha_per_field.  U is updated
+ * in place. */
 int or_step(const or_problem *P, double *U, double dt);
 
 /* The same step with the splitting constants alpha given for all three
@@ -88,6 +108,9 @@ int or_step(const or_problem *P, double *U, double dt);
  * grid must be stepped with the full grid's alpha); alpha_per_stage is not
  * consulted. */
 int or_step_alpha(const or_problem *P, double *U, double dt, const double *alpha);
+
+/* The same with per-field splitting constants (layout of or_alpha_fields). */
+int or_step_alpha_fields(const or_problem *P, double *U, double dt, const double *alpha_f);
 
 /* Advance to t_end.  dt = cfl / sum_d(alpha_d/dx_d) when dt_fixed <= 0,
  * else dt = dt_fixed; the last step is shortened to land on t_end.  Stops
