@@ -61,8 +61,14 @@ enum { ENOAO_FP64 = 0, ENOAO_FP32_BULK = 1 };
 /* When alpha of the Lax-Friedrichs splitting (Sec. 2: the maximum of |f'(u)|
  * over the mesh) is taken for the Euler equations: once per step from U^n
  * for all three Runge-Kutta stages (the default), or per stage from that
- * stage's input state.  dt always follows the CFL rule with alpha of U^n. */
-enum { ENOAO_ALPHA_PER_STEP = 0, ENOAO_ALPHA_PER_STAGE = 1 };
+ * stage's input state.  PER_FIELD: once per step from U^n, but each
+ * characteristic field k splits with its own alpha_k = max |lambda_k| (per axis
+ * max |u_d - c|, max |u_d| for the entropy and shear fields, max |u_d + c|),
+ * the component-wise reading; single-problem contexts only (batched contexts
+ * and enoao_step_noalloc return ENOAO_EINVAL), and FP32 bulk then re-decides
+ * its near-ties inside the sweep whatever enoao_set_redecide says.  dt always
+ * follows the CFL rule with alpha = max |u_d| + c of U^n. */
+enum { ENOAO_ALPHA_PER_STEP = 0, ENOAO_ALPHA_PER_STAGE = 1, ENOAO_ALPHA_PER_FIELD = 2 };
 
 typedef struct {
   int ndim;        /* 1, 2 or 3 */
@@ -75,7 +81,7 @@ typedef struct {
   double lo[3];    /* domain [lo, hi] per axis; dx = (hi - lo) / n */
   double hi[3];
   int bc[3];       /* ENOAO_PERIODIC or ENOAO_TRANSMISSIVE (zero-gradient) per axis */
-  int alpha_mode;  /* ENOAO_ALPHA_PER_STEP or ENOAO_ALPHA_PER_STAGE */
+  int alpha_mode;  /* ENOAO_ALPHA_PER_STEP, _PER_STAGE or _PER_FIELD */
   double adv_speed;  /* scalar advection speed a */
   double gamma;      /* ratio of specific heats (Euler) */
   double delta;      /* selection threshold, 1e-5 in the paper (Sec. 3.2 remark) */

@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "enoao.h")
 SCALAR_ADVECTION, EULER = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 FP64, FP32_BULK = 0, 1
-ALPHA_PER_STEP, ALPHA_PER_STAGE = 0, 1
+ALPHA_PER_STEP, ALPHA_PER_STAGE, ALPHA_PER_FIELD = 0, 1, 2
 REDECIDE_AUTO, REDECIDE_IN_SWEEP, REDECIDE_GRID = 0, 1, 2
 
 STATUS = {0: "ENOAO_OK", 1: "ENOAO_EINVAL", 2: "ENOAO_ENOMEM", 3: "ENOAO_ECUDA",

@@ -61,8 +61,9 @@ constexpr double kInf = std::numeric_limits<double>::infinity();
 // Euler equations |u_d| + c per axis) into alpha_acc[slot], plus the
 // non-physical check.
 __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int ndim, int nv,
-                             double gamma, StepState* st, int slot) {
+                             double gamma, StepState* st, int slot, int field) {
   double amax[3] = {0, 0, 0};
+  double af[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // per field: |u-c|, |u|, |u+c|
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
     const double rho = U[i];
@@ -76,7 +77,21 @@ __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int 
       continue;
     }
     const double cs = sqrt(gamma * p * ir);
-    for (int d = 0; d < ndim; ++d) amax[d] = fmax(amax[d], fabs(U[(1 + d) * ncell + i]) * ir + cs);
+    for (int d = 0; d < ndim; ++d) {
+      amax[d] = fmax(amax[d], fabs(U[(1 + d) * ncell + i]) * ir + cs);
+      if (field) {
+        const double u = U[(1 + d) * ncell + i] * ir;
+        af[d][0] = fmax(af[d][0], fabs(u - cs));
+        af[d][1] = fmax(af[d][1], fabs(u));
+        af[d][2] = fmax(af[d][2], fabs(u + cs));
+      }
+    }
+  }
+  if (field) {  // rare option: one atomic per thread and value
+    for (int d = 0; d < ndim; ++d)
+      for (int k = 0; k < 3; ++k)
+        if (af[d][k] > 0.0)
+          atomicMax(&st->alpha_acc_f[slot][d][k], (unsigned long long)__double_as_longlong(af[d][k]));
   }
   __shared__ double red[3][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -99,6 +114,7 @@ __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int 
 
 struct StepConsts {
   int system, ndim;
+  int field;  // per-field splitting constants (Euler)
   double adv_speed;
   double dx[3];
 };
@@ -110,6 +126,27 @@ __device__ void finalize_pending(StepState* st) {
     if (st->last) st->done = 1;
     st->pending = 0;
   }
+}
+
+// Per-field constants of the step from the running maxima of slot cur (the
+// one-alpha value, for dt, is the largest of them); clear: the other slot too.
+// alpha of axis d for the CFL rule (Euler): |u_d| + c of slot cur, which per
+// field is the larger of max |u_d - c| and max |u_d + c| (the last stage then
+// accumulates only the per-field maxima).
+__device__ double step_alpha(const StepState* st, const StepConsts& k, int cur, int d) {
+  if (k.field)
+    return fmax(__longlong_as_double((long long)st->alpha_acc_f[cur][d][0]),
+                __longlong_as_double((long long)st->alpha_acc_f[cur][d][2]));
+  return __longlong_as_double((long long)st->alpha_acc[cur][d]);
+}
+
+__device__ void load_field_alpha(StepState* st, const StepConsts& k, int cur, bool clear) {
+  if (!k.field) return;
+  for (int d = 0; d < 3; ++d)
+    for (int f = 0; f < 3; ++f) {
+      st->alpha_f[d][f] = d < k.ndim ? __longlong_as_double((long long)st->alpha_acc_f[cur][d][f]) : 0.0;
+      if (clear) st->alpha_acc_f[cur ^ 1][d][f] = 0ull;
+    }
 }
 
 // Start of a step: finalise the previous one, fix alpha from U^n and dt from
@@ -125,13 +162,14 @@ __global__ void step_begin_kernel(StepState* st, StepConsts k) {
   double s = 0.0;
   for (int d = 0; d < k.ndim; ++d) {
     const double a = k.system == ENOAO_EULER
-                         ? __longlong_as_double((long long)st->alpha_acc[cur][d])
+                         ? step_alpha(st, k, cur, d)
                          : fabs(k.adv_speed);
     st->alpha[d] = a;
     s += a / k.dx[d];
   }
   st->par = cur ^ 1;
   for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = st->alpha_stage[d] = 0ull;
+  load_field_alpha(st, k, cur, true);
   double dt = st->dt_fixed > 0.0 ? st->dt_fixed : st->cfl / s;
   st->last = 0;
   if (st->t + dt >= st->t_end) {
@@ -143,6 +181,7 @@ __global__ void step_begin_kernel(StepState* st, StepConsts k) {
 }
 
 __global__ void finalize_kernel(StepState* st) { finalize_pending(st); }
+
 
 // Per-stage alpha: the next stage splits with the alpha of the state the
 // previous stage wrote (accumulated by that stage's last sweep).
@@ -162,10 +201,11 @@ __global__ void manual_stage_kernel(StepState* st, StepConsts k, int stage, doub
     const int cur = (int)(st->steps & 1);
     for (int d = 0; d < k.ndim; ++d)
       st->alpha[d] = k.system == ENOAO_EULER
-                         ? __longlong_as_double((long long)st->alpha_acc[cur][d])
+                         ? step_alpha(st, k, cur, d)
                          : fabs(k.adv_speed);
     st->par = cur ^ 1;
     for (int d = 0; d < 3; ++d) st->alpha_acc[cur ^ 1][d] = st->alpha_stage[d] = 0ull;
+    load_field_alpha(st, k, cur, true);
     st->last = 0;
     st->pending = 0;
   }
@@ -179,8 +219,9 @@ __global__ void alpha_current_kernel(StepState* st, StepConsts k) {
   const int cur = (int)(st->steps & 1);
   for (int d = 0; d < k.ndim; ++d)
     st->alpha[d] = k.system == ENOAO_EULER
-                       ? __longlong_as_double((long long)st->alpha_acc[cur][d])
+                       ? step_alpha(st, k, cur, d)
                        : fabs(k.adv_speed);
+  load_field_alpha(st, k, cur, false);
   st->skip = 0;
 }
 
@@ -208,6 +249,7 @@ StepConsts consts(const enoao_ctx* c) {
   StepConsts k;
   k.system = c->cfg.system;
   k.ndim = c->cfg.ndim;
+  k.field = c->cfg.system == ENOAO_EULER && c->cfg.alpha_mode == ENOAO_ALPHA_PER_FIELD;
   k.adv_speed = c->cfg.adv_speed;
   for (int d = 0; d < 3; ++d) k.dx[d] = c->dx[d];
   return k;
@@ -252,6 +294,7 @@ enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
 // sweep's tiles (enoao_set_redecide; AUTO currently re-decides in the sweep).
 bool use_list(const enoao_ctx* c) {
   if (!fp32(c) || c->batch || c->redecide != ENOAO_REDECIDE_GRID) return false;
+  if (consts(c).field) return false;  // per-field splitting re-decides in the sweep
   long long faces = 0;
   for (int d = 0; d < c->cfg.ndim; ++d)
     faces = std::max(faces, c->ncell / c->cfg.n[d] * (c->cfg.n[d] + 1));
@@ -341,19 +384,29 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   const int block = c->block[d];
   int per_sm = 1;
   cudaError_t e;
+  const int nv = c->nv, order = c->cfg.order;
+  a.field = consts(c).field;
   if (fp32(c)) {
-    e = sweep_configure_fp32(c->nv, c->cfg.order, smem);
-    if (e == cudaSuccess) e = sweep_occupancy_fp32(c->nv, c->cfg.order, block, smem, &per_sm);
+    e = a.field ? sweep_configure_fp32_field(nv, order, smem) : sweep_configure_fp32(nv, order, smem);
+    if (e == cudaSuccess)
+      e = a.field ? sweep_occupancy_fp32_field(nv, order, block, smem, &per_sm)
+                  : sweep_occupancy_fp32(nv, order, block, smem, &per_sm);
   } else {
-    e = sweep_configure_fp64(c->nv, c->cfg.order, smem);
-    if (e == cudaSuccess) e = sweep_occupancy_fp64(c->nv, c->cfg.order, block, smem, &per_sm);
+    e = a.field ? sweep_configure_fp64_field(nv, order, smem) : sweep_configure_fp64(nv, order, smem);
+    if (e == cudaSuccess)
+      e = a.field ? sweep_occupancy_fp64_field(nv, order, block, smem, &per_sm)
+                  : sweep_occupancy_fp64(nv, order, block, smem, &per_sm);
   }
   if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "sweep setup: %s", cudaGetErrorString(e));
   if (per_sm < 1) return fail(c, ENOAO_EINVAL, "sweep tile does not fit on an SM");
   long long grid = std::min<long long>(a.ntiles, (long long)c->sms * per_sm);
   if (grid < 1) grid = 1;
-  e = fp32(c) ? sweep_launch_fp32(c->nv, c->cfg.order, a, (int)grid, block, smem, c->s)
-              : sweep_launch_fp64(c->nv, c->cfg.order, a, (int)grid, block, smem, c->s);
+  if (a.field)
+    e = fp32(c) ? sweep_launch_fp32_field(nv, order, a, (int)grid, block, smem, c->s)
+                : sweep_launch_fp64_field(nv, order, a, (int)grid, block, smem, c->s);
+  else
+    e = fp32(c) ? sweep_launch_fp32(nv, order, a, (int)grid, block, smem, c->s)
+                : sweep_launch_fp64(nv, order, a, (int)grid, block, smem, c->s);
   if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
   if (after_sweep) CU(c, cudaEventRecord(after_sweep, c->s));
   if (list) {
@@ -522,8 +575,12 @@ static enoao_status validate(const enoao_config* cfg, bool batched) {
     return fail(nullptr, ENOAO_EINVAL, "gamma must exceed 1");
   if (!(cfg->delta >= 0.0)) return fail(nullptr, ENOAO_EINVAL, "delta must be >= 0");
   if (!(cfg->tie_rel >= 0.0)) return fail(nullptr, ENOAO_EINVAL, "tie_rel must be >= 0");
-  if (cfg->alpha_mode != ENOAO_ALPHA_PER_STEP && cfg->alpha_mode != ENOAO_ALPHA_PER_STAGE)
-    return fail(nullptr, ENOAO_EINVAL, "alpha_mode must be ENOAO_ALPHA_PER_STEP or _PER_STAGE");
+  if (cfg->alpha_mode != ENOAO_ALPHA_PER_STEP && cfg->alpha_mode != ENOAO_ALPHA_PER_STAGE &&
+      cfg->alpha_mode != ENOAO_ALPHA_PER_FIELD)
+    return fail(nullptr, ENOAO_EINVAL,
+                "alpha_mode must be ENOAO_ALPHA_PER_STEP, _PER_STAGE or _PER_FIELD");
+  if (batched && cfg->alpha_mode == ENOAO_ALPHA_PER_FIELD)
+    return fail(nullptr, ENOAO_EINVAL, "per-field alpha is not available for batched contexts");
   return ENOAO_OK;
 }
 
@@ -642,7 +699,7 @@ enoao_status enoao_init_state(enoao_ctx* c, const double* U, int on_device) {
   if (c->cfg.system == ENOAO_EULER) {
     const int blocks = std::max(1, std::min<int>((int)((c->ncell + 255) / 256), c->sms * 8));
     alpha_kernel<<<blocks, 256, 0, c->s>>>(c->U[0], c->ncell, c->cfg.ndim, c->nv, c->cfg.gamma,
-                                           c->st, 0);
+                                           c->st, 0, consts(c).field);
   }
   CU(c, cudaGetLastError());
   r = leave(c);

@@ -37,6 +37,9 @@ struct StepState {
                                       // state stage 0 or 1 writes (bit patterns)
   unsigned int redo_epoch;        // sweeps that listed faces: tags the changed-face marks
   unsigned int redo_done;         // blocks of the running apply pass that have left it
+  // per-field alpha (Euler): per axis max |u_d - c|, max |u_d|, max |u_d + c|
+  double alpha_f[3][3];                   // of the current step
+  unsigned long long alpha_acc_f[2][3][3];  // running maxima (bit patterns), as alpha_acc
 };
 
 
@@ -79,7 +82,7 @@ struct SweepArgs {
   int stage;            // Runge-Kutta stage 0..2
   int ta, ts;           // tile: lines x faces
   int se;               // shared-memory row pitch in cells (sweep_row_pitch)
-  int pad_se;
+  int field;            // 1: per-field splitting constants (st->alpha_f), Euler only
   long long tiles_s;    // tiles along dir
   long long tiles_a;    // tiles across the line index
   long long tiles_b;    // tiles along the remaining axis (dir != 0)
@@ -106,6 +109,15 @@ cudaError_t sweep_configure_fp32(int nv, int order, size_t smem);
 cudaError_t sweep_occupancy_fp64(int nv, int order, int block, size_t smem, int* per_sm);
 cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm);
 cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cudaStream_t s);
+// per-field splitting constants (a.field; Euler systems, nv 3..5)
+cudaError_t sweep_launch_fp64_field(int nv, int order, const SweepArgs& a, int grid, int block,
+                                    size_t smem, cudaStream_t s);
+cudaError_t sweep_launch_fp32_field(int nv, int order, const SweepArgs& a, int grid, int block,
+                                    size_t smem, cudaStream_t s);
+cudaError_t sweep_configure_fp64_field(int nv, int order, size_t smem);
+cudaError_t sweep_configure_fp32_field(int nv, int order, size_t smem);
+cudaError_t sweep_occupancy_fp64_field(int nv, int order, int block, size_t smem, int* per_sm);
+cudaError_t sweep_occupancy_fp32_field(int nv, int order, int block, size_t smem, int* per_sm);
 
 // Raises a kernel's dynamic shared-memory limit to at least smem, never
 // lowers it: the limit belongs to the kernel, not to one launch, and the

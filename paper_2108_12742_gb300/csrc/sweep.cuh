@@ -746,6 +746,33 @@ __device__ __forceinline__ void split_diff(const double (&qa64)[NV], const doubl
   }
 }
 
+// The same pair of cells for per-field splitting: dF/2 and dq/2 (exact
+// halvings), to be split per characteristic field after the projection.
+template <int NV, typename R>
+__device__ __forceinline__ void split_parts(const double (&qa64)[NV], const double (&qb64)[NV],
+                                            const R (&qa)[NV], R gm1, R adv, R (&hdF)[NV],
+                                            R (&hdq)[NV]) {
+  R qb[NV], dq[NV], dF[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    qb[c] = to_bulk<R>(qb64[c]);
+    dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
+  }
+  flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    hdF[c] = R(0.5) * dF[c];
+    hdq[c] = R(0.5) * dq[c];
+  }
+}
+
+// Per-field splitting constant of characteristic field v (u-c, entropy,
+// shear..., u+c) along axis dir: max |u_d - c|, max |u_d|, max |u_d + c|.
+template <int NV>
+__device__ __forceinline__ double field_alpha(const StepState* st, int dir, int v) {
+  return st->alpha_f[dir][v == 0 ? 0 : (v == NV - 1 ? 2 : 1)];
+}
+
 // FP32 bulk: the state is checked, and the next step's alpha taken, on each
 // step's final state; the kinetic energy, sound speed and |u| + c are FP32,
 // the energy difference E - ke stays FP64.  The alpha of a later stage of the
@@ -807,13 +834,62 @@ __device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long c
   }
 }
 
+// Per-field variant (last stage only): the state check, and per axis the
+// maxima of |u_d - c|, |u_d| and |u_d + c| in amax[3 d + 0..2], in FP32 like
+// the one-alpha path's |u_d| + c.
+template <int NV>
+__device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long cell,
+                                                 const double (&unew)[NV], int mode,
+                                                 double (&amax)[9]) {
+  StepState* st = A.st;
+  if (A.stage != 2) return;
+  if constexpr (NV > 1) {
+    const float rho = f32_rn(unew[0]);
+    float m2 = 0.0f;
+#pragma unroll
+    for (int c = 1; c < NV - 1; ++c) {
+      const float m = f32_rn(unew[c]);
+      m2 += m * m;
+    }
+    const float ke = __fdividef(0.5f * m2, rho);
+    const float p = f32_rn((A.gamma - 1.0) * (unew[NV - 1] - f64_of(ke)));
+    const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
+    if (!ok) {
+      atomicOr(&st->err, kErrNonPhys);
+      atomicMin(&st->err_cell, cell);
+    } else if (mode & kModeAlpha) {
+      const float ir = __fdividef(1.0f, rho);
+      const float cs = sqrtf((float)A.gamma * p * ir);
+#pragma unroll
+      for (int d = 0; d < NV - 2; ++d) {
+        const float u = f32_rn(unew[1 + d]) * ir;
+        const double lam[3] = {f64_of(fabsf(u - cs)), f64_of(fabsf(u)), f64_of(fabsf(u + cs))};
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (okey(lam[k]) > okey(amax[3 * d + k])) amax[3 * d + k] = lam[k];
+      }
+    }
+  }
+}
+
+// Number of alpha maxima a sweep accumulates: |u_d| + c per axis, or with
+// per-field constants |u_d - c|, |u_d|, |u_d + c| per axis.
+template <bool FIELD>
+constexpr int kAmax = FIELD ? 9 : 3;
+
 // One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
 // constant of the swept axis and the step size; amax accumulates |u_d| + c of
-// combined states (last stage), nfall counts FP64 re-decisions.
-template <int NV, int ORDER, typename R, bool COHERENT = false, bool DEFER = false>
+// combined states (last stage), nfall counts FP64 re-decisions.  FIELD: each
+// characteristic field splits with its own constant (st->alpha_f): phase 1
+// keeps dF/2 and dq/2, the split follows the projection, and the face's
+// centre part 1/2 R diag(alpha) L dq moves into its correction C.
+template <int NV, int ORDER, typename R, bool COHERENT = false, bool DEFER = false,
+          bool FIELD = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
                                            unsigned char* smem_raw, double alpha_d, double dt,
-                                           double (&amax)[3], unsigned long long& nfall) {
+                                           double (&amax)[kAmax<FIELD>],
+                                           unsigned long long& nfall) {
+  static_assert(!FIELD || NV >= 3, "per-field constants are for the Euler equations");
   using GE = Geo<ORDER>;
   constexpr int G = GE::G;
   constexpr bool FP32 = sizeof(R) == 4;
@@ -833,6 +909,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const bool sfast = dir == 0;
   const R alpha = (R)alpha_d;
   const R halpha = R(0.5) * alpha;
+  // splitting constant of field v: alpha, or per field max |u_d - c|, |u_d|, |u_d + c|
+  R alo = alpha, amid = alpha, ahi = alpha;
+  if constexpr (FIELD) {
+    alo = (R)st->alpha_f[A.dir][0];
+    amid = (R)st->alpha_f[A.dir][1];
+    ahi = (R)st->alpha_f[A.dir][2];
+  }
+  auto afield = [&](int v) { return v == 0 ? alo : (v == NV - 1 ? ahi : amid); };
+  // the same in FP64, for the re-decisions of near-ties
+  auto alpha64 = [&](int v) {
+    if constexpr (FIELD) return field_alpha<NV>(st, A.dir, v);
+    return alpha_d;
+  };
   const R gm1 = (R)(A.gamma - 1.0);
   const R adv = (R)A.adv_speed;
   const R delta = (R)A.delta;
@@ -904,11 +993,59 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       }
     }
   };
+  // Per-field windows: dfp / dfm hold dF/2 and dq/2; field v splits after the
+  // projection, d = L dF/2 +- alpha_v L dq/2 (sign 0: +, sign 1: mirrored -),
+  // with magnitude sum |L||dF/2| + alpha_v sum |L||dq/2| for the near-tie bound.
+  auto window_field = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R av,
+                          R (&d)[8], R (&m)[8]) {
+    const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+    const R sa = sgn == 0 ? av : -av;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = m[i] = R(0);
+#pragma unroll
+    for (int i = GE::LO; i <= GE::HI; ++i) {
+      const int e = sidx(a, sgn == 0 ? j - 4 + i : j + 4 - i);
+      R xF[NV], xq[NV];
+      CV::load(dfp, cells, e, xF);
+      CV::load(dfm, cells, e, xq);
+      R aF = R(0), aq = R(0), mF = R(0), mq = R(0);
+      if constexpr (NV >= 4) {
+        if (shear) {
+          const R fv = shear_comp<NV>(xF, v), qv = shear_comp<NV>(xq, v);
+          aF = fv - w * xF[0];
+          aq = qv - w * xq[0];
+          if constexpr (FP32) {
+            mF = rabs(fv) + rabs(w) * rabs(xF[0]);
+            mq = rabs(qv) + rabs(w) * rabs(xq[0]);
+          }
+        }
+      }
+      if (!shear) {
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+          aF += L[c] * xF[c];
+          aq += L[c] * xq[c];
+          if constexpr (FP32) {
+            mF += rabs(L[c]) * rabs(xF[c]);
+            mq += rabs(L[c]) * rabs(xq[c]);
+          }
+        }
+      }
+      const R acc = fma(sa, aq, aF);
+      d[i] = sgn == 0 ? acc : -acc;
+      m[i] = fma(av, mq, mF);
+    }
+  };
   // Projected window of field v (the same arithmetic in phase 2 and in the
   // phase-2b check of a flagged choice, which must reproduce its pick).
-  auto field_window = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R (&d)[8],
+  auto field_window = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R av, R (&d)[8],
                           R (&mag)[8]) {
     const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+    if constexpr (FIELD) {
+      window_field(a, j, sgn, v, L, w, av, d, mag);
+      return;
+    }
+    (void)av;
     if (shear) {
       window_shear(a, j, sgn, v, w, d, mag);
     } else if constexpr (FP32) {
@@ -947,7 +1084,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         double qb64[NV];
         load_state<NV, COHERENT>(A.u_in, A.cstride, la + sb * g.stride_d, dir, qb64);
         R fp[NV], fm[NV];
-        split_diff<NV, R>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
+        if constexpr (FIELD)
+          split_parts<NV, R>(qa64, qb64, qa, gm1, adv, fp, fm);  // dF/2, dq/2
+        else
+          split_diff<NV, R>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
         CV::store(dfp, cells, si, fp);
         CV::store(dfm, cells, si, fm);
       }
@@ -987,10 +1127,25 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
         // f^+ then mirrored f^- window, one live at a time
         R cv = R(0);
+        const R av = afield(v);
+        if constexpr (FIELD) {
+          // the face's centre part: - alpha_v L dq/2 of the face's own pair
+          R xq[NV];
+          CV::load(dfm, cells, sidx(a, j), xq);
+          R aq = R(0);
+          if constexpr (NV >= 4) {
+            if (shear) aq = shear_comp<NV>(xq, v) - w * xq[0];
+          }
+          if (!shear) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) aq += L[c] * xq[c];
+          }
+          cv = -av * aq;
+        }
 #pragma unroll
         for (int sgn = 0; sgn < 2; ++sgn) {
           R d[8], mag[8];
-          field_window(a, j, sgn, v, L, w, d, mag);
+          field_window(a, j, sgn, v, L, w, av, d, mag);
           int pick;
           bool marg = false;
           R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
@@ -1099,7 +1254,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           const int kk = __ffs(todo) - 1;
           todo &= todo - 1;
           const int pick = redo_lane<NV, ORDER, COHERENT>(A, g, al, g.s0 + f - 1, kk >> 1, kk & 1,
-                                                          alpha_d);
+                                                          alpha64(kk >> 1));
           picks |= (unsigned long long)pick << (4 * kk);
           ++nfall;
         }
@@ -1121,7 +1276,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           gf = 0;
         }
         const int pick = redo_group<NV, ORDER, COHERENT, W>(A, g, ga, g.s0 + gf - 1, k >> 1, k & 1,
-                                                            alpha_d, lane & (W - 1));
+                                                            alpha64(k >> 1), lane & (W - 1));
         // my rank among the lanes with work tells which group (if any) took it
         const int rank = __popc(have & ((1u << lane) - 1u));
         const int mine = __shfl_sync(FULL, pick, (rank < NG ? rank : 0) * W);
@@ -1160,7 +1315,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           L[0] = R(1);
         }
         R d[8], mag[8];
-        field_window(al, j, sgn, v, L, w, d, mag);
+        field_window(al, j, sgn, v, L, w, afield(v), d, mag);
         int pick_old;
         bool m;
         const R nomx[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -1219,9 +1374,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       CV::load(Cf, cells, sidx(a, j), Cv);
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
-        const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
-        const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
-        A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + to_f64(Cv[c]);
+        if constexpr (FIELD) {
+          // F^ = (F_l + F_r)/2 + C, the split's centre part being inside C
+          A.fhat[perm_comp<NV>(c, dir) * nf + fc] = 0.5 * (Fl[c] + Fr[c]) + to_f64(Cv[c]);
+        } else {
+          const double fp = 0.5 * (Fl[c] + alpha_d * ql[c]);
+          const double fm = 0.5 * (Fr[c] - alpha_d * qr[c]);
+          A.fhat[perm_comp<NV>(c, dir) * nf + fc] = fp + fm + to_f64(Cv[c]);
+        }
       }
     });
   } else {
@@ -1231,8 +1391,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       const int e = G + t;
       const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
       R r[NV], p0[NV], m1[NV], c1[NV], c0[NV];
+      // per field: dF/2 of both of the cell's pairs (the centre part is in C)
       CV::load(dfp, cells, sidx(a, e - 1), p0);
-      CV::load(dfm, cells, sidx(a, e), m1);
+      CV::load(FIELD ? dfp : dfm, cells, sidx(a, e), m1);
       CV::load(Cf, cells, sidx(a, e), c1);
       CV::load(Cf, cells, sidx(a, e - 1), c0);
 #pragma unroll
@@ -1288,7 +1449,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         } else if (mode & kModeAlpha) {
           const double cs = sqrt(A.gamma * p * ir);
 #pragma unroll
-          for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
+          for (int d = 0; d < NV - 2; ++d) {
+            if constexpr (FIELD) {
+              const double u = unew[1 + d] * ir;
+              amax[3 * d] = fmax(amax[3 * d], fabs(u - cs));
+              amax[3 * d + 1] = fmax(amax[3 * d + 1], fabs(u));
+              amax[3 * d + 2] = fmax(amax[3 * d + 2], fabs(u + cs));
+            } else {
+              amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
+            }
+          }
         }
       } else {
         if (!isfinite(unew[0])) {
@@ -1311,13 +1481,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #ifndef ENOAO_FP32_MIN_BLOCKS_AO7
 #define ENOAO_FP32_MIN_BLOCKS_AO7 5
 #endif
-template <int ORDER, typename R>
+// Per-field splitting keeps two projections per window cell live and takes
+// four blocks (128 registers).
+template <int ORDER, typename R, bool FIELD = false>
 constexpr int sweep_min_blocks() {
-  return sizeof(R) == 8 ? 1 : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5 : ENOAO_FP32_MIN_BLOCKS_AO7);
+  return sizeof(R) == 8 ? 1
+                        : (FIELD ? 4
+                                 : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5
+                                               : ENOAO_FP32_MIN_BLOCKS_AO7));
 }
 
-template <int NV, int ORDER, typename R, bool DEFER = false>
-__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
+template <int NV, int ORDER, typename R, bool DEFER = false, bool FIELD = false>
+__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD>())
     sweep_kernel(const SweepArgs A) {
   constexpr bool FP32 = sizeof(R) == 4;
   StepState* st = A.st;
@@ -1326,7 +1501,10 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
   const int mode = A.mode;
   const double alpha_d = st->alpha[A.dir];
   const double dt = st->dt;
-  double amax[3] = {0.0, 0.0, 0.0};
+  constexpr int KA = kAmax<FIELD>;
+  double amax[KA];
+#pragma unroll
+  for (int i = 0; i < KA; ++i) amax[i] = 0.0;
   unsigned long long nfall = 0;
   // Dynamic tile queue: tiles differ in cost (FP64 re-decisions cluster at
   // discontinuities), so blocks pull the next tile instead of striding.  The
@@ -1337,7 +1515,8 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
     __syncthreads();
     const long long tile = s_tile;
     if (tile >= A.ntiles) break;
-    sweep_tile<NV, ORDER, R, false, DEFER>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax, nfall);
+    sweep_tile<NV, ORDER, R, false, DEFER, FIELD>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax,
+                                                   nfall);
   }
   if (threadIdx.x == 0) {
     __threadfence();
@@ -1358,11 +1537,12 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
     if (nfall) atomicAdd(&st->fallbacks, nfall);
   }
   if (NV > 1 && (mode & kModeAlpha)) {
-    // block max of |u_d| + c, then one atomic per block and axis
-    __shared__ double red[3][32];
+    // block max of |u_d| + c (per field: |u_d - c|, |u_d|, |u_d + c|), then
+    // one atomic per block and value
+    __shared__ double red[KA][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < KA; ++d) {
       double v = amax[d];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -1372,13 +1552,21 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R>())
     if (threadIdx.x < 32) {
       const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
+      for (int d = 0; d < KA; ++d) {
         double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        unsigned long long* acc = A.stage == 2 ? st->alpha_acc[st->par] : st->alpha_stage;
-        if (threadIdx.x == 0 && d < A.ndim && v > 0.0)
-          atomicMax(&acc[d], (unsigned long long)__double_as_longlong(v));
+        unsigned long long* acc;
+        int axis;
+        if constexpr (FIELD) {  // last stage only (per-field runs with per-step alpha)
+          acc = &st->alpha_acc_f[st->par][0][0] + d;
+          axis = d / 3;
+        } else {
+          acc = (A.stage == 2 ? st->alpha_acc[st->par] : st->alpha_stage) + d;
+          axis = d;
+        }
+        if (threadIdx.x == 0 && axis < A.ndim && v > 0.0)
+          atomicMax(acc, (unsigned long long)__double_as_longlong(v));
       }
     }
   }
