@@ -571,6 +571,44 @@ def run_paper_cases(args):
            "note": "value: all FP32-bulk runs together, cell-stage updates per host second"})
 
 
+def run_adr(args):
+    """The ADR spectral-analysis tool (Sec. 4.1): modified wavenumbers of
+    ENO-AO5 and ENO-AO7 at amplitude 1 for every mode k = 1 .. N/2 of an N-cell
+    periodic grid, all modes in one flux sweep; timed end to end on the host
+    clock (H2D of the modes, the sweep, D2H of the fluxes, the FFT) and the
+    sweep kernel alone with CUDA events."""
+    import torch
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import adr
+    n = args.adr_n
+    out = {}
+    for order in (5, 7):
+        for pname, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
+            adr.adr(n=256, order=order, precision=prec)  # warm-up (build, first launch)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            theta, kp = adr.adr(n=n, order=order, precision=prec)
+            sec = time.perf_counter() - t0
+            k, _, U = adr.modes(n)
+            with eno.Solver((n, k.size), (0.0, 0.0), (float(n), float(k.size)),
+                            system=eno.SCALAR_ADVECTION, order=order, bc=eno.PERIODIC,
+                            adv_speed=1.0, precision=prec) as s:
+                s.init_state(U)
+                kms = s.time_sweep(0, 3)
+            out[f"ao{order}_{pname}"] = {"modes_per_s": theta.size / sec, "seconds": sec,
+                                         "kernel_ms": kms, "kappa": kp}
+    d5 = float(np.abs(out["ao5_fp32_bulk"]["kappa"] - out["ao5_fp64"]["kappa"]).max())
+    d7 = float(np.abs(out["ao7_fp32_bulk"]["kappa"] - out["ao7_fp64"]["kappa"]).max())
+    for v in out.values():
+        del v["kappa"]
+    _line(f"adr-{n}-modes", out["ao5_fp64"]["modes_per_s"], 1e3 * out["ao5_fp64"]["seconds"], 1, 1,
+          {"config": {"workload": f"ADR of ENO-AO5/AO7, {n // 2} cosine modes of amplitude 1 on "
+                                  f"{n} periodic cells, one sweep"},
+           "unit": "modes/s", "dtype": "f64",
+           "unit_note": "value: ENO-AO5 FP64 modes per host second, end to end",
+           "results": out, "max_abs_kappa_fp32_bulk_vs_fp64": {"ao5": d5, "ao7": d7}})
+
+
 def run_tie_study(args):
     """FP32-bulk near-tie margin study: for each tie_rel, the stencil choices of
     the FP32-bulk path against the FP64 path (itself oracle-identical) on
@@ -632,7 +670,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="euler2d",
                     choices=["euler2d", "batched", "euler3d", "euler1d", "advection",
-                             "tie-study", "paper-cases"])
+                             "tie-study", "paper-cases", "adr"])
+    ap.add_argument("--adr-n", type=int, default=4096)
     ap.add_argument("--paper-n2d", type=int, default=800)
     ap.add_argument("--tie-n", type=int, default=2048)
     ap.add_argument("--tie-evolve", type=int, default=200)
@@ -651,6 +690,8 @@ def main():
         return run_small(args, args.workload)
     if args.workload == "tie-study":
         return run_tie_study(args)
+    if args.workload == "adr":
+        return run_adr(args)
     if args.workload == "paper-cases":
         return run_paper_cases(args)
     return run_gpu(args)
