@@ -113,6 +113,8 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   if (cfg->order != 5 && cfg->order != 7) return nofail(ENOAO_EINVAL, "order must be 5 or 7");
   if (cfg->precision != ENOAO_FP64 && cfg->precision != ENOAO_FP32_BULK)
     return nofail(ENOAO_EINVAL, "unknown precision");
+  if (cfg->alpha_mode == ENOAO_ALPHA_PER_FIELD)
+    return nofail(ENOAO_EINVAL, "per-field alpha is not available in the allocation-free step");
   if (cfg->alpha_mode != ENOAO_ALPHA_PER_STEP && cfg->alpha_mode != ENOAO_ALPHA_PER_STAGE)
     return nofail(ENOAO_EINVAL, "unknown alpha_mode");
   if (cfg->bc[0] != ENOAO_PERIODIC && cfg->bc[0] != ENOAO_TRANSMISSIVE)
