@@ -46,3 +46,16 @@ def test_product_path_does_not_reach_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "liboracle" not in text, f
+
+
+def test_configurations_are_validated_before_any_device_call(lib):
+    # rejected on the host with ENOAO_EINVAL and a message, whether or not a GPU exists
+    with pytest.raises(eno.EnoaoError) as e:
+        eno.Solver((16,), (0.0,), (1.0,), alpha_mode=3)
+    assert e.value.status == 1 and "alpha_mode" in str(e.value)
+    with pytest.raises(eno.EnoaoError) as e:
+        eno.Batch([16, 20], [0.0, 0.0], [1.0, 1.0], alpha_mode=eno.ALPHA_PER_FIELD)
+    assert e.value.status == 1 and "per-field" in str(e.value)
+    with pytest.raises(eno.EnoaoError) as e:
+        eno.Solver((16,), (0.0,), (1.0,), order=6)
+    assert e.value.status == 1
