@@ -70,6 +70,7 @@ def _load():
             lib.or_candidate_flux.argtypes = [D, ctypes.c_int]
             lib.or_euler_eigen.argtypes = [ctypes.c_int, ctypes.c_double, D,
                                            ctypes.c_double, D, D]
+            lib.or_roe_average.argtypes = [D, D, ctypes.c_int, ctypes.c_double, D, D]
             lib.or_alpha.argtypes = [P, D, D]
             lib.or_alpha_fields.argtypes = [P, D, D]
             lib.or_fluxes_fields.argtypes = [P, D, ctypes.c_int, D, D,
@@ -166,6 +167,17 @@ def euler_eigen(ndim, gamma, vel, H):
     v = np.ascontiguousarray(vel, dtype=np.float64)
     _load().or_euler_eigen(ndim, gamma, _dp(v), H, _dp(R), _dp(L))
     return R, L
+
+
+def roe_average(ndim, gamma, ql, qr):
+    """Roe-averaged (velocity[ndim], H) of two conserved Euler states."""
+    ql = np.ascontiguousarray(ql, dtype=np.float64)
+    qr = np.ascontiguousarray(qr, dtype=np.float64)
+    assert ql.shape == qr.shape == (ndim + 2,)
+    vel = np.zeros(ndim)
+    H = ctypes.c_double()
+    _load().or_roe_average(_dp(ql), _dp(qr), ndim, gamma, _dp(vel), ctypes.byref(H))
+    return vel, H.value
 
 
 def alpha(P, U):

@@ -67,6 +67,11 @@ double or_candidate_flux(const double *fj, int c);
 void or_euler_eigen(int ndim, double gamma, const double *vel, double H,
                     double *R, double *L);
 
+/* Roe average (velocity[ndim], H) of two Euler states ql, qr = (rho,
+ * momenta..., E) at the face between them (Sec. 4). */
+void or_roe_average(const double *ql, const double *qr, int ndim, double gamma,
+                    double *vel, double *H);
+
 /* Lax-Friedrichs alpha per axis (max over the mesh of |df/du|). */
 int or_alpha(const or_problem *P, const double *U, double *alpha);
 
