@@ -235,18 +235,25 @@ int enoao_uses_grid_redecide(const enoao_ctx *ctx);
  *   U_in   : device pointer, U^n as [nv][n] float64 (not modified).
  *   U_out  : device pointer, receives U^{n+1} in the same layout; may equal
  *            U_in.
- *   dt     : step size; alpha is computed from U_in (Sec. 2).
+ *   dt     : step size; alpha is computed from U_in.
  *   stream : cudaStream_t the work is ordered on (0 = legacy default).
+ * U_in and U_out must be device memory of the current device (checked:
+ * ENOAO_EINVAL otherwise); their size cannot be checked from a pointer, so
+ * each must hold nv * n[0] doubles.
  * The two intermediate stage states and the step's device-side state live in
- * one fixed file-scope device array (12 MiB, held on every GPU that loads the
- * library until the process exits).  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call shares the array and finds the previous
- * call's contents there (whatever must start at zero is cleared by the call),
- * so calls that overlap on the GPU -- from other streams or threads -- race:
- * serialise them.  The call waits for its stream to finish the step and
- * returns ENOAO_ENONPHYS for rho <= 0, p <= 0 or NaN; messages are read with
- * enoao_last_error(NULL). */
+ * one fixed file-scope device array (12 MiB per GPU, held until the process
+ * exits).  The first call on a device loads the library's device code there
+ * (CUDA loads modules lazily by default), which brings the array into
+ * existence, and looks up its device address (cudaGetSymbolAddress); make
+ * that first call during set-up, before any stream capture.  The address is
+ * kept for the life of the process, so do not use this entry point on a
+ * device after cudaDeviceReset.  Every call shares the array and finds the
+ * previous call's contents there (whatever must start at zero is cleared by
+ * the call), so calls that overlap on the GPU -- from other streams or
+ * threads -- race: serialise them.  The call waits for its stream to finish
+ * the step and returns ENOAO_ENONPHYS for rho <= 0, p <= 0 or NaN (with the
+ * first such cell in the message) and ENOAO_ETIMEOUT when a bounded device
+ * wait gave up; messages are read with enoao_last_error(NULL). */
 enoao_status enoao_step_noalloc(const enoao_config *cfg, const double *U_in, double *U_out,
                                 double dt, void *cuda_stream);
 

@@ -158,10 +158,28 @@ def step_noalloc(cfg, U_in, U_out, dt, stream=None):
     U_in / U_out are CUDA tensors shaped (nv, n) or (nv, 1, 1, n); the library
     allocates nothing for the step (its stage states live in a fixed device
     array of at most 2^18 cells)."""
+    nv = 3 if cfg.system == EULER else 1
+    n = int(cfg.n[0])
+    for name, U in (("U_in", U_in), ("U_out", U_out)):
+        # the C side reads and writes nv * n doubles through these pointers:
+        # check everything it cannot see before any device call
+        if not _is_torch(U):
+            raise ValueError(f"{name} must be a CUDA torch tensor")
+        if tuple(U.shape) not in ((nv, n), (nv, 1, 1, n)):
+            raise ValueError(f"{name} has shape {tuple(U.shape)}; expected ({nv}, {n})")
+        if str(U.dtype) != "torch.float64":
+            raise ValueError(f"{name} has dtype {U.dtype}; expected torch.float64")
+        if not U.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if not U.is_cuda:
+            raise ValueError(f"{name} must be on the GPU (enoao_step_noalloc takes device buffers)")
+        import torch
+        if U.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on cuda:{U.device.index}, not the current device "
+                             f"cuda:{torch.cuda.current_device()}")
     lib = load()
-    pi, di = _ptr(U_in)
-    po, do = _ptr(U_out)
-    assert di and do, "enoao_step_noalloc takes device buffers"
+    pi, _ = _ptr(U_in)
+    po, _ = _ptr(U_out)
     st = lib.enoao_step_noalloc(ctypes.byref(cfg), pi, po, dt, _stream_handle(stream))
     if st:
         raise EnoaoError(st, lib.enoao_last_error(None).decode())

@@ -132,6 +132,23 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   if (cfg->system == ENOAO_EULER && !(cfg->gamma > 1.0)) return nofail(ENOAO_EINVAL, "gamma must exceed 1");
   if (!(dt > 0.0)) return nofail(ENOAO_EINVAL, "dt must be positive");
 
+  // both states must be device memory of the current device (a host pointer
+  // handed to the kernels would fault or silently read the wrong memory)
+  {
+    int cur = 0;
+    cudaError_t pe = cudaGetDevice(&cur);
+    const double* ptrs[2] = {U_in, U_out};
+    for (int k = 0; k < 2 && pe == cudaSuccess; ++k) {
+      cudaPointerAttributes pa;
+      pe = cudaPointerGetAttributes(&pa, ptrs[k]);
+      if (pe != cudaSuccess) break;
+      if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != cur)
+        return nofail(ENOAO_EINVAL, std::string(k ? "U_out" : "U_in") +
+                                        " is not device memory of the current device");
+    }
+    if (pe != cudaSuccess)
+      return nofail(ENOAO_ECUDA, std::string("pointer check: ") + cudaGetErrorString(pe));
+  }
   double* scratch = nullptr;
   enoao_status r = scratch_for_current_device(&scratch);
   if (r != ENOAO_OK) return r;
@@ -212,5 +229,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   if (err & kErrNonPhys)
     return nofail(ENOAO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) at cell " +
                                       std::to_string(cell));
+  if (err & kErrTimeout) return nofail(ENOAO_ETIMEOUT, "device wait timed out");
+  if (err & kErrRedoFull) return nofail(ENOAO_ECUDA, "internal error: re-decision list overflow");
   return ENOAO_OK;
 }

@@ -59,3 +59,27 @@ def test_configurations_are_validated_before_any_device_call(lib):
     with pytest.raises(eno.EnoaoError) as e:
         eno.Solver((16,), (0.0,), (1.0,), order=6)
     assert e.value.status == 1
+
+
+def test_noalloc_step_checks_its_buffers_before_any_device_call(lib, monkeypatch):
+    # enoao_step_noalloc reads and writes nv * n doubles through raw pointers;
+    # the binding rejects what the C side cannot see (size, dtype, layout,
+    # host memory) before the call is made
+    torch = pytest.importorskip("torch")
+    called = []
+    monkeypatch.setattr(lib, "enoao_step_noalloc", lambda *a: called.append(a) or 0)
+    n = 64
+    cfg = eno.make_config((n,), (0.0,), (1.0,), system=eno.EULER, order=5)
+    good = torch.zeros((3, n), dtype=torch.float64)
+    bad = [
+        (torch.zeros((3, n - 1), dtype=torch.float64), "shape"),
+        (torch.zeros((1, n), dtype=torch.float64), "shape"),
+        (torch.zeros((3, n), dtype=torch.float32), "dtype"),
+        (torch.zeros((n, 3), dtype=torch.float64).t(), "contiguous"),
+        (good, "GPU"),                       # right layout, but host memory
+        (good.numpy(), "CUDA torch tensor"),
+    ]
+    for U, what in bad:
+        with pytest.raises(ValueError, match=what):
+            eno.step_noalloc(cfg, U, U, 1e-4)
+    assert not called
