@@ -222,6 +222,16 @@ enoao_status enoao_set_redecide(enoao_ctx *ctx, int mode);
 /* 1 when the context's steps use the grid-wide pass, else 0. */
 int enoao_uses_grid_redecide(const enoao_ctx *ctx);
 
+/* Fault-injection knob for tests (the paper has no counterpart): bounds the
+ * passes in which a warp re-decides its flagged FP32-bulk choices inside the
+ * sweep (the default, -1, is 64 nv passes, which every warp needs at most
+ * 2 nv of).  A warp that reaches a smaller bound stops waiting, keeps the FP32
+ * pick of the choices left and sets the device error word, so that the next
+ * synchronising call returns ENOAO_ETIMEOUT; nothing traps and the context
+ * stays usable (enoao_init_state clears the error).  ENOAO_EINVAL for
+ * batched contexts and for limits below -1. */
+enoao_status enoao_set_redecide_pass_limit(enoao_ctx *ctx, int passes);
+
 /* One third-order TVD Runge-Kutta step of a 1D problem that allocates no
  * device memory.  The paper has no counterpart: this is a deployment aid for
  * callers that cannot let a library allocate -- applications that reserve
@@ -263,6 +273,19 @@ enoao_status enoao_step_noalloc(const enoao_config *cfg, const double *U_in, dou
  * mean duration of one launch in milliseconds.  The state U^n is not
  * modified (stage 0 writes U1). */
 enoao_status enoao_time_sweep(enoao_ctx *ctx, int dir, int nrep, float *ms_per_launch);
+
+/* Measurement helper (the paper has no counterpart): the arithmetic peak the
+ * roofline of the sweep kernels divides by.  kind ENOAO_PEAK_FP32 (scalar
+ * FP32 fused multiply-add), ENOAO_PEAK_FP32X2 (packed pairs, two per
+ * instruction) or ENOAO_PEAK_FP64.  Every thread of a grid of 8 blocks of 256
+ * threads per SM runs 8 independent multiply-add chains for trips x 64 steps;
+ * one warm-up launch, then one launch timed with CUDA events on cuda_stream.
+ * Returns the rate in TFLOP/s (2 flops per multiply-add) and the launch time
+ * in ms, at whatever clock the GPU ran (no clock is set).  Allocates 8 MiB of
+ * scratch for the duration of the call.  ENOAO_EINVAL for an unknown kind. */
+enum { ENOAO_PEAK_FP32 = 0, ENOAO_PEAK_FP32X2 = 1, ENOAO_PEAK_FP64 = 2 };
+enoao_status enoao_measure_fma_peak(int kind, int trips, void *cuda_stream, double *tflops,
+                                    float *ms);
 
 /* Times every supported tile shape of every axis on the current state
  * (restored afterwards) with CUDA events and keeps the fastest. */

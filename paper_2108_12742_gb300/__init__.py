@@ -99,12 +99,16 @@ def load():
         "enoao_set_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "enoao_set_redecide": (ctypes.c_int, [P, ctypes.c_int]),
         "enoao_uses_grid_redecide": (ctypes.c_int, [P]),
+        "enoao_set_redecide_pass_limit": (ctypes.c_int, [P, ctypes.c_int]),
         "enoao_get_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
         "enoao_autotune": (ctypes.c_int, [P]),
         "enoao_time_sweep": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_float)]),
         "enoao_step_noalloc": (ctypes.c_int, [C, P, P, ctypes.c_double, P]),
+        "enoao_measure_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P,
+                                                  ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -183,6 +187,20 @@ def step_noalloc(cfg, U_in, U_out, dt, stream=None):
     st = lib.enoao_step_noalloc(ctypes.byref(cfg), pi, po, dt, _stream_handle(stream))
     if st:
         raise EnoaoError(st, lib.enoao_last_error(None).decode())
+
+
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64 = 0, 1, 2
+
+
+def measure_fma_peak(kind, trips=1000, stream=None):
+    """(TFLOP/s, ms) of the multiply-add microbenchmark of the given kind."""
+    lib = load()
+    tf, ms = ctypes.c_double(), ctypes.c_float()
+    st = lib.enoao_measure_fma_peak(kind, trips, _stream_handle(stream), ctypes.byref(tf),
+                                    ctypes.byref(ms))
+    if st:
+        raise EnoaoError(st, "enoao_measure_fma_peak failed")
+    return tf.value, ms.value
 
 
 class Solver:
@@ -296,6 +314,10 @@ class Solver:
         """Where FP32-bulk near-ties are re-decided in FP64: REDECIDE_AUTO,
         REDECIDE_IN_SWEEP or REDECIDE_GRID (the grid-wide pass after each sweep)."""
         self._check(self._lib.enoao_set_redecide(self._h, mode))
+
+    def set_redecide_pass_limit(self, passes):
+        """Test knob: bound on the in-sweep FP64 re-decision passes (-1: default)."""
+        self._check(self._lib.enoao_set_redecide_pass_limit(self._h, passes))
 
     def uses_grid_redecide(self):
         return bool(self._lib.enoao_uses_grid_redecide(self._h))

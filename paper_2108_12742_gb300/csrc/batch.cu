@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
     A.adv_speed = B.adv_speed;
     A.delta = B.delta;
     A.tie_rel = B.tie_rel;
+    A.redo_passes = 64 * NV;
 
     // alpha of the initial state of this launch
     double alpha;
@@ -102,14 +103,19 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
       double a = 0.0;
       const double* U = B.U[0] + off;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double rho = __ldcg(U + i), m = __ldcg(U + B.total + i), E = __ldcg(U + 2 * B.total + i);
-        const double pr = (B.gamma - 1.0) * (E - 0.5 * m * m / rho);
-        if (!(rho > 0.0) || !(pr > 0.0) || !isfinite(pr)) {
+        // the speeds as a step's last stage takes them (FP32 bulk: speeds32),
+        // so that launches split anywhere give the same run
+        double u[NV], sp[3];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) u[c] = __ldcg(U + c * B.total + i);
+        const bool ok = sizeof(R) == 4 ? speeds32<NV, false>(u, B.gamma, sp)
+                                       : speeds64<NV, false>(u, B.gamma, sp);
+        if (!ok) {
           atomicOr(&B.st->err, kErrNonPhys);
           atomicMin(&B.st->err_cell, off + i);
           continue;
         }
-        a = fmax(a, fabs(m / rho) + sqrt(B.gamma * pr / rho));
+        a = fmax(a, sp[0]);
       }
       alpha = block_max(a, s_red);
     } else {

@@ -15,6 +15,7 @@
 #include "enoao.h"
 #include "enoao_ctx.h"
 #include "enoao_internal.h"
+#include "state_speed.cuh"
 
 using namespace enoao;
 
@@ -58,40 +59,44 @@ constexpr double kInf = std::numeric_limits<double>::infinity();
 // ---------------------------------------------------------------- small kernels
 
 // alpha of the current state (Sec. 2: max of |f'(u)| over the mesh; for the
-// Euler equations |u_d| + c per axis) into alpha_acc[slot], plus the
-// non-physical check.
-__global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int ndim, int nv,
-                             double gamma, StepState* st, int slot, int field) {
+// Euler equations |u_d| + c per axis) into alpha_acc[slot] (and the per-field
+// maxima into alpha_acc_f[slot] with FIELD), plus the non-physical check.
+// BULK takes the speeds with the FP32 bulk arithmetic of a step's last stage
+// (speeds32), so that a step from a state set here takes the same alpha as
+// the uninterrupted run did.
+template <int NV, bool BULK, bool FIELD>
+__global__ void alpha_kernel(const double* __restrict__ U, long long ncell, double gamma,
+                             StepState* st, int slot) {
+  constexpr int ND = NV - 2;
   double amax[3] = {0, 0, 0};
-  double af[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // per field: |u-c|, |u|, |u+c|
+  double af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * blockDim.x) {
-    const double rho = U[i];
-    const double ir = 1.0 / rho;  // one FP64 division per cell (GB300's FP64 unit is slow)
-    double m2 = 0.0;
-    for (int c = 1; c < nv - 1; ++c) m2 += U[c * ncell + i] * U[c * ncell + i];
-    const double p = (gamma - 1.0) * (U[(nv - 1) * ncell + i] - 0.5 * m2 * ir);
-    if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p)) {
+    double u[NV];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) u[c] = U[c * ncell + i];
+    double s[3];
+    const bool ok = BULK ? speeds32<NV, false>(u, gamma, s) : speeds64<NV, false>(u, gamma, s);
+    if (!ok) {
       atomicOr(&st->err, kErrNonPhys);
       atomicMin(&st->err_cell, i);
       continue;
     }
-    const double cs = sqrt(gamma * p * ir);
-    for (int d = 0; d < ndim; ++d) {
-      amax[d] = fmax(amax[d], fabs(U[(1 + d) * ncell + i]) * ir + cs);
-      if (field) {
-        const double u = U[(1 + d) * ncell + i] * ir;
-        af[d][0] = fmax(af[d][0], fabs(u - cs));
-        af[d][1] = fmax(af[d][1], fabs(u));
-        af[d][2] = fmax(af[d][2], fabs(u + cs));
+#pragma unroll
+    for (int d = 0; d < ND; ++d) amax[d] = fmax(amax[d], s[d]);
+    if constexpr (FIELD) {
+      double sf[9];
+      if (BULK ? speeds32<NV, true>(u, gamma, sf) : speeds64<NV, true>(u, gamma, sf)) {
+#pragma unroll
+        for (int k = 0; k < 3 * ND; ++k) af[k] = fmax(af[k], sf[k]);
       }
     }
   }
-  if (field) {  // rare option: one atomic per thread and value
-    for (int d = 0; d < ndim; ++d)
-      for (int k = 0; k < 3; ++k)
-        if (af[d][k] > 0.0)
-          atomicMax(&st->alpha_acc_f[slot][d][k], (unsigned long long)__double_as_longlong(af[d][k]));
+  if constexpr (FIELD) {  // rare option: one atomic per thread and value
+#pragma unroll
+    for (int k = 0; k < 3 * ND; ++k)
+      if (af[k] > 0.0)
+        atomicMax(&st->alpha_acc_f[slot][k / 3][k % 3], (unsigned long long)__double_as_longlong(af[k]));
   }
   __shared__ double red[3][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -106,10 +111,34 @@ __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, int 
     for (int d = 0; d < 3; ++d) {
       double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
       for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (threadIdx.x == 0 && d < ndim && v > 0.0)
+      if (threadIdx.x == 0 && d < ND && v > 0.0)
         atomicMax(&st->alpha_acc[slot][d], (unsigned long long)__double_as_longlong(v));
     }
   }
+}
+
+template <int NV>
+void launch_alpha_nv(const double* U, long long ncell, double gamma, StepState* st, int slot,
+                     bool bulk, bool field, int blocks, cudaStream_t s) {
+  if (bulk) {
+    if (field)
+      alpha_kernel<NV, true, true><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+    else
+      alpha_kernel<NV, true, false><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+  } else {
+    if (field)
+      alpha_kernel<NV, false, true><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+    else
+      alpha_kernel<NV, false, false><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+  }
+}
+
+// Launches alpha_kernel for an Euler state of nv = 3, 4 or 5 variables.
+void launch_alpha(int nv, const double* U, long long ncell, double gamma, StepState* st, int slot,
+                  bool bulk, bool field, int blocks, cudaStream_t s) {
+  if (nv == 3) launch_alpha_nv<3>(U, ncell, gamma, st, slot, bulk, field, blocks, s);
+  if (nv == 4) launch_alpha_nv<4>(U, ncell, gamma, st, slot, bulk, field, blocks, s);
+  if (nv == 5) launch_alpha_nv<5>(U, ncell, gamma, st, slot, bulk, field, blocks, s);
 }
 
 struct StepConsts {
@@ -380,6 +409,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.adv_speed = c->cfg.adv_speed;
   a.delta = c->cfg.delta;
   a.tie_rel = c->cfg.tie_rel;
+  a.redo_passes = c->redo_passes >= 0 ? c->redo_passes : 64 * c->nv;
   const size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts, a.se);
   const int block = c->block[d];
   int per_sm = 1;
@@ -698,8 +728,8 @@ enoao_status enoao_init_state(enoao_ctx* c, const double* U, int on_device) {
   reset_state_kernel<<<1, 1, 0, c->s>>>(c->st);
   if (c->cfg.system == ENOAO_EULER) {
     const int blocks = std::max(1, std::min<int>((int)((c->ncell + 255) / 256), c->sms * 8));
-    alpha_kernel<<<blocks, 256, 0, c->s>>>(c->U[0], c->ncell, c->cfg.ndim, c->nv, c->cfg.gamma,
-                                           c->st, 0, consts(c).field);
+    launch_alpha(c->nv, c->U[0], c->ncell, c->cfg.gamma, c->st, 0, fp32(c), consts(c).field != 0,
+                 blocks, c->s);
   }
   CU(c, cudaGetLastError());
   r = leave(c);
@@ -907,6 +937,18 @@ enoao_status enoao_set_redecide(enoao_ctx* c, int mode) {
 }
 
 int enoao_uses_grid_redecide(const enoao_ctx* c) { return c && use_list(c) ? 1 : 0; }
+
+enoao_status enoao_set_redecide_pass_limit(enoao_ctx* c, int passes) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  if (passes < -1) return fail(c, ENOAO_EINVAL, "pass limit must be >= 0, or -1 for the default");
+  c->redo_passes = passes;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return ENOAO_OK;
+}
 
 enoao_status enoao_set_tiles(enoao_ctx* c, int dir, int ta, int ts) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");

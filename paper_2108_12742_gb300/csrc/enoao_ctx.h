@@ -45,4 +45,5 @@ struct enoao_ctx {
   float* redo_dc = nullptr;            // nv per slot
   unsigned* redo_mark = nullptr;       // per face
   long long redo_cap = 0;
+  int redo_passes = -1;                // in-sweep re-decision pass bound (-1: 64 nv)
 };

@@ -83,6 +83,8 @@ struct SweepArgs {
   int ta, ts;           // tile: lines x faces
   int se;               // shared-memory row pitch in cells (sweep_row_pitch)
   int field;            // 1: per-field splitting constants (st->alpha_f), Euler only
+  int redo_passes;      // FP32 bulk: bound on the in-sweep re-decision passes of a warp
+                        // round; reaching it sets kErrTimeout (64 nv by default)
   long long tiles_s;    // tiles along dir
   long long tiles_a;    // tiles across the line index
   long long tiles_b;    // tiles along the remaining axis (dir != 0)

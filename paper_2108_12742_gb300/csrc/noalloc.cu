@@ -15,6 +15,7 @@
 
 #include "enoao.h"
 #include "enoao_internal.h"
+#include "state_speed.cuh"
 
 namespace enoao {
 void set_thread_error(const char* msg);
@@ -54,22 +55,26 @@ __global__ void noalloc_begin_kernel(StepState* st, double dt) {
   st->par = 1;
 }
 
+// alpha with the operations the regular path uses (state_speed.cuh): FP32
+// bulk speeds for the step's U^n alpha in FP32 bulk (bulk = 1), FP64 speeds
+// otherwise and for the per-stage alphas of both precisions.
 __global__ void noalloc_alpha_kernel(const double* __restrict__ U, long long n, int nv,
-                                     double gamma, double adv, StepState* st) {
+                                     double gamma, double adv, StepState* st, int bulk) {
   double a = 0.0;
   if (nv == 1) {
     a = fabs(adv);
   } else {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-      const double rho = U[i], m = U[n + i], E = U[2 * n + i];
-      const double p = (gamma - 1.0) * (E - 0.5 * (m * m) / rho);
-      if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p)) {
+      const double u[3] = {U[i], U[n + i], U[2 * n + i]};
+      double s[3];
+      const bool ok = bulk ? speeds32<3, false>(u, gamma, s) : speeds64<3, false>(u, gamma, s);
+      if (!ok) {
         atomicOr(&st->err, kErrNonPhys);
         atomicMin(&st->err_cell, i);
         continue;
       }
-      a = fmax(a, fabs(m / rho) + sqrt(gamma * p / rho));
+      a = fmax(a, s[0]);
     }
   }
   for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
@@ -163,7 +168,8 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
 
   noalloc_begin_kernel<<<1, 1, 0, s>>>(st, dt);
   const int ablocks = (int)std::min<long long>((n + 255) / 256, 64);
-  noalloc_alpha_kernel<<<ablocks, 256, 0, s>>>(U_in, n, nv, cfg->gamma, cfg->adv_speed, st);
+  noalloc_alpha_kernel<<<ablocks, 256, 0, s>>>(U_in, n, nv, cfg->gamma, cfg->adv_speed, st,
+                                               cfg->precision == ENOAO_FP32_BULK);
   noalloc_alpha_set_kernel<<<1, 1, 0, s>>>(st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return nofail(ENOAO_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
@@ -191,6 +197,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   a.adv_speed = cfg->adv_speed;
   a.delta = cfg->delta;
   a.tie_rel = cfg->tie_rel;
+  a.redo_passes = 64 * nv;
   const size_t smem = sweep_smem_bytes(nv, cfg->order, f32, a.ta, a.ts, a.se);
   const int block = 128;
   int per_sm = 1;
@@ -208,7 +215,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   for (int stage = 0; stage < 3; ++stage) {
     if (stage > 0 && per_stage) {
       // this stage splits with the alpha of its own input state
-      noalloc_alpha_kernel<<<ablocks, 256, 0, s>>>(ins[stage], n, nv, cfg->gamma, cfg->adv_speed, st);
+      noalloc_alpha_kernel<<<ablocks, 256, 0, s>>>(ins[stage], n, nv, cfg->gamma, cfg->adv_speed, st, 0);
       noalloc_alpha_set_kernel<<<1, 1, 0, s>>>(st);
     }
     a.u_in = ins[stage];

@@ -33,6 +33,7 @@
 #include <cstdint>
 
 #include "enoao_internal.h"
+#include "state_speed.cuh"
 
 namespace enoao {
 
@@ -101,32 +102,6 @@ __device__ __forceinline__ float okey(float a) { return a; }
 template <typename R>
 __device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; }
 
-// Conversions between FP64 and FP32 on the integer units.  The hardware
-// conversion instructions issue to the FP64 unit, which the FP32 bulk path
-// otherwise leaves to the state update; these give the same bits for every
-// value of normal FP32 magnitude.
-// f32_rn: round to nearest even at mantissa bit 29 (the carry runs into the
-// exponent); magnitudes below the smallest normal float give a signed zero,
-// magnitudes from 2^128 up, infinities and NaN give NaN.
-__device__ __forceinline__ float f32_rn(double x) {
-  const unsigned lo = __double2loint(x), hi = __double2hiint(x);
-  const unsigned long long b =
-      ((static_cast<unsigned long long>(hi) << 32) | lo) + (0x0FFFFFFFull + ((lo >> 29) & 1u));
-  unsigned r = static_cast<unsigned>(b >> 29) - (896u << 23);  // exponent bias 1023 -> 127
-  r = (r & 0x7FFFFFFFu) | (hi & 0x80000000u);
-  const unsigned e = (hi >> 20) & 0x7FFu;
-  if (e - 897u > 253u) r = e < 897u ? (hi & 0x80000000u) : 0x7FC00000u;
-  return __uint_as_float(r);
-}
-// f64_of: exact widening; zero and subnormal floats give a signed zero,
-// infinities and NaN give NaN.
-__device__ __forceinline__ double f64_of(float x) {
-  const unsigned u = __float_as_uint(x), a = u & 0x7FFFFFFFu;
-  unsigned hi = (a >> 3) + (896u << 20), lo = u << 29;  // exponent bias 127 -> 1023
-  if (a < 0x00800000u) hi = lo = 0u;
-  if (a >= 0x7F800000u) hi = 0x7FF80000u, lo = 0u;
-  return __hiloint2double(static_cast<int>(hi | (u & 0x80000000u)), static_cast<int>(lo));
-}
 // FP64 value in the bulk precision, and a bulk value widened to FP64.
 template <typename R>
 __device__ __forceinline__ R to_bulk(double x);
@@ -786,46 +761,27 @@ __device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long c
   StepState* st = A.st;
   if constexpr (NV > 1) {
     if (A.stage < 2 && (mode & kModeAlpha)) {
-      const double rho = unew[0], ir = 1.0 / rho;
-      double m2 = 0.0;
-#pragma unroll
-      for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
-      const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 * ir);
-      if (!(rho > 0.0 && p > 0.0 && isfinite(p))) {
+      double s[3];
+      if (!speeds64<NV, false>(unew, A.gamma, s)) {
         atomicOr(&st->err, kErrNonPhys);
         atomicMin(&st->err_cell, cell);
       } else {
-        const double cs = sqrt(A.gamma * p * ir);
 #pragma unroll
-        for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
+        for (int d = 0; d < NV - 2; ++d) amax[d] = fmax(amax[d], s[d]);
       }
       return;
     }
   }
   if (A.stage == 2) {
     if constexpr (NV > 1) {
-      const float rho = f32_rn(unew[0]);
-      float m2 = 0.0f;
-#pragma unroll
-      for (int c = 1; c < NV - 1; ++c) {
-        const float m = f32_rn(unew[c]);
-        m2 += m * m;
-      }
-      const float ke = __fdividef(0.5f * m2, rho);
-      const float p = f32_rn((A.gamma - 1.0) * (unew[NV - 1] - f64_of(ke)));
-      const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
-      if (!ok) {
+      double s[3];
+      if (!speeds32<NV, false>(unew, A.gamma, s)) {
         atomicOr(&st->err, kErrNonPhys);
         atomicMin(&st->err_cell, cell);
       } else if (mode & kModeAlpha) {
-        const float ir = __fdividef(1.0f, rho);
-        const float cs = sqrtf((float)A.gamma * p * ir);
 #pragma unroll
-        for (int d = 0; d < NV - 2; ++d) {
-          // non-negative: the bit patterns order like the values
-          const double s = f64_of(fabsf(f32_rn(unew[1 + d])) * ir + cs);
-          if (okey(s) > okey(amax[d])) amax[d] = s;
-        }
+        for (int d = 0; d < NV - 2; ++d)
+          if (okey(s[d]) > okey(amax[d])) amax[d] = s[d];  // non-negative: bits order like values
       }
     } else if (!isfinite(unew[0])) {
       atomicOr(&st->err, kErrNonPhys);
@@ -844,30 +800,14 @@ __device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long c
   StepState* st = A.st;
   if (A.stage != 2) return;
   if constexpr (NV > 1) {
-    const float rho = f32_rn(unew[0]);
-    float m2 = 0.0f;
-#pragma unroll
-    for (int c = 1; c < NV - 1; ++c) {
-      const float m = f32_rn(unew[c]);
-      m2 += m * m;
-    }
-    const float ke = __fdividef(0.5f * m2, rho);
-    const float p = f32_rn((A.gamma - 1.0) * (unew[NV - 1] - f64_of(ke)));
-    const bool ok = rho > 0.0f && p > 0.0f && isfinite(p);
-    if (!ok) {
+    double s[9];
+    if (!speeds32<NV, true>(unew, A.gamma, s)) {
       atomicOr(&st->err, kErrNonPhys);
       atomicMin(&st->err_cell, cell);
     } else if (mode & kModeAlpha) {
-      const float ir = __fdividef(1.0f, rho);
-      const float cs = sqrtf((float)A.gamma * p * ir);
 #pragma unroll
-      for (int d = 0; d < NV - 2; ++d) {
-        const float u = f32_rn(unew[1 + d]) * ir;
-        const double lam[3] = {f64_of(fabsf(u - cs)), f64_of(fabsf(u)), f64_of(fabsf(u + cs))};
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (okey(lam[k]) > okey(amax[3 * d + k])) amax[3 * d + k] = lam[k];
-      }
+      for (int k = 0; k < 3 * (NV - 2); ++k)
+        if (okey(s[k]) > okey(amax[k])) amax[k] = s[k];
     }
   }
 }
@@ -1233,13 +1173,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       const int f = e0 + rd * estep;
       const bool valid = f < cnt && g.a0 + al < g.na;
       const int j = G - 1 + f;
-      const unsigned fix = valid ? fixmask[sidx(al, j)] : 0u;
+      unsigned fix = valid ? fixmask[sidx(al, j)] : 0u;
       if (!__any_sync(FULL, fix != 0u)) continue;
       // Re-decide every flagged choice of the warp: in each pass, group gi
       // takes the lowest flagged choice of the gi-th lane that still has one,
       // and that lane collects the result from group gi.  Every pass clears at
-      // least one of the at most 32 * 2 NV flags, so the pass bound is never
-      // reached; if it were, the error word says so.
+      // least one of the at most 32 * 2 NV flags, so the default bound (64 NV
+      // passes) is never reached; a smaller bound (a test knob) can be: then
+      // the error word says so and the choices left keep their FP32 pick.
       constexpr int NG = 32 / W;
       unsigned todo = fix;
       unsigned long long picks = 0ull;
@@ -1259,10 +1200,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           ++nfall;
         }
       }
-      for (int pass = 0; pass < 64 * NV + 1; ++pass) {
+      const int pass_limit = A.redo_passes;
+      for (int pass = 0; pass <= pass_limit; ++pass) {
         const unsigned have = __ballot_sync(FULL, todo != 0u);
         if (!have) break;
-        if (pass == 64 * NV) {
+        if (pass == pass_limit) {
           if (lane == 0) atomicOr(&st->err, kErrTimeout);
           break;
         }
@@ -1287,6 +1229,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           ++nfall;
         }
       }
+      fix &= ~todo;  // choices left by a pass bound keep their FP32 pick
       if (!fix) continue;
       // apply the changed choices of this face
       Eigen<NV, R> E;
@@ -1437,28 +1380,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         bulk_state_check<NV>(A, cell, unew, mode, amax);
       } else if constexpr (NV > 1) {
         // non-physical check and next-step alpha on the new state
-        const double rho = unew[0], ir = 1.0 / rho;  // one FP64 division per cell
-        double m2 = 0.0;
-#pragma unroll
-        for (int c = 1; c < NV - 1; ++c) m2 += unew[c] * unew[c];
-        const double p = (A.gamma - 1.0) * (unew[NV - 1] - 0.5 * m2 * ir);
-        const bool ok = rho > 0.0 && p > 0.0 && isfinite(p);
-        if (!ok) {
+        double s[kAmax<FIELD>];
+        if (!speeds64<NV, FIELD>(unew, A.gamma, s)) {
           atomicOr(&st->err, kErrNonPhys);
           atomicMin(&st->err_cell, cell);
         } else if (mode & kModeAlpha) {
-          const double cs = sqrt(A.gamma * p * ir);
 #pragma unroll
-          for (int d = 0; d < NV - 2; ++d) {
-            if constexpr (FIELD) {
-              const double u = unew[1 + d] * ir;
-              amax[3 * d] = fmax(amax[3 * d], fabs(u - cs));
-              amax[3 * d + 1] = fmax(amax[3 * d + 1], fabs(u));
-              amax[3 * d + 2] = fmax(amax[3 * d + 2], fabs(u + cs));
-            } else {
-              amax[d] = fmax(amax[d], fabs(unew[1 + d]) * ir + cs);
-            }
-          }
+          for (int k = 0; k < (FIELD ? 3 : 1) * (NV - 2); ++k) amax[k] = fmax(amax[k], s[k]);
         }
       } else {
         if (!isfinite(unew[0])) {

@@ -409,7 +409,15 @@ def test_stages_match_oracle_on_their_own_inputs(name, precision, redecide, alph
             G.append(s.get_stage_state(k + 1) if k < 2 else s.get_state())
             a_used = np.asarray(oracle.alpha(P, G[k])) if per_stage else a0
             nd = len(shape)
-            assert np.allclose(s.stats().alpha[:nd], a_used[:nd], rtol=1e-12, atol=0), k
+            # FP32 bulk takes the step's alpha (stage 0, or every stage with one
+            # alpha per step) from FP32 characteristic speeds, as a step's last
+            # stage does; the reference then applies the alpha the path took
+            fp32_alpha = precision == eno.FP32_BULK and (k == 0 or not per_stage)
+            a_path = np.array(s.stats().alpha[:])
+            assert np.allclose(a_path[:nd], a_used[:nd], rtol=1e-6 if fp32_alpha else 1e-12,
+                               atol=0), k
+            if fp32_alpha:
+                a_used = a_path
             Lk = oracle.rhs(P, G[k], a_used)
             if k == 0:
                 ref = U + dt * Lk
