@@ -34,7 +34,10 @@ N_CELLS = 4096
 CFL = 0.5
 SEED = 1
 METRIC = "ENO-AO cell-stage updates/s (FP64 vs FP32-mixed) + L1 err vs FP64 oracle"
-FLOPS_PER_FACE = 885        # FP32 flops of one face of one axis (2D Euler, ENO-AO5)
+FLOPS_PER_FACE = 1150       # flops of one face of one axis, 2D Euler ENO-AO5 (the method's
+                            # operation count: split, Roe eigen-system, projection of both
+                            # windows, indicators, selection, back-projection)
+FLOPS_PER_FACE_COUNTED = 885  # the same path counted operation by operation in the kernel
 BYTES_PER_CELL_Y = 32 + 16 + 32  # y sweep, stage 0: read U^n (FP64) and L_x (FP32), write U1 (FP64)
 WORKLOAD = "euler2d-4096x4096-quadrant-riemann-ao5"
 
@@ -127,6 +130,43 @@ def measured_peaks():
         with open(p) as fh:
             return json.load(fh), "measured"
     return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_model():
+    """Model name of the host CPU (x86 'model name', else Arm implementer/part)."""
+    try:
+        text = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    import re
+    m = re.search(r"^model name\s*:\s*(.+)$", text, re.M)
+    if m:
+        return m.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", text, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", text, re.M)
+    names = {("0x41", "0xd4f"): "Arm Neoverse V2 (NVIDIA Grace)"}
+    if imp and part:
+        return names.get((imp.group(1), part.group(1)),
+                         f"Arm implementer {imp.group(1)} part {part.group(1)}")
+    return "unknown"
+
+
+def measure_peaks(local):
+    """FP32, packed-FP32 and FP64 multiply-add peaks of this GPU from the
+    library's microbenchmark, with the SM clock sampled while it runs."""
+    import paper_2108_12742_gb300 as eno
+    out = {}
+    clk = ClockSampler(local)
+    clk.start()
+    for kind, name, trips in ((eno.PEAK_FP32, "fp32", 4000), (eno.PEAK_FP32X2, "fp32x2", 2000),
+                              (eno.PEAK_FP64, "fp64", 200)):
+        best = 0.0
+        for _ in range(3):
+            tf, _ = eno.measure_fma_peak(kind, trips)
+            best = max(best, tf)
+        out[name] = best
+    out["clocks"] = clk.stop()
+    return out
 
 
 def profiled_traffic(summary):
@@ -254,7 +294,10 @@ def run_gpu(args):
     # ---- FP64
     k64 = max(1, min(args.steps, args.fp64_steps))
     s64 = make(eno.FP64)
+    clk64 = ClockSampler(local)
+    clk64.start()
     ms64 = timed(s64, k64)
+    clocks64 = clk64.stop()
     k_ms64 = [s64.time_sweep(d, 2) for d in range(2)]
     # ---- L1 difference FP32-bulk vs FP64 after the same number of steps
     s32.init_state(dev_U0)
@@ -271,6 +314,7 @@ def run_gpu(args):
     linf = [float(diff[v].max() / b[v].abs().max()) for v in range(4)]
     decisions = 2 * 4 * 3 * 2 * cells  # fields x signs x stages x axes per step (faces ~ cells)
     fallback_rate = st32.fp64_fallbacks / max(1, decisions * (st32.steps))
+    evolved64 = b.cpu().numpy() if rank == 0 and not args.no_cpu else None
 
     # ---- end to end through the public API with host buffers (FP32-bulk)
     host_in = torch.from_numpy(U0).pin_memory()
@@ -294,38 +338,56 @@ def run_gpu(args):
     # share of a step in the launch list): it adds L_x, combines and, on the
     # last stage, checks the state and takes the next alpha.  It is timed alone
     # right after the timed region on the library's stream (CUDA events on
-    # that stream), stage 0 in the mode it has inside a step.  Algorithmic
-    # work per face: 885 FP32 flops (2D Euler, ENO-AO5); bytes per cell: read
-    # U^n (4 x 8 B) and L_x (4 x 4 B), write U1 (4 x 8 B).
+    # that stream), stage 0 in the mode it has inside a step.  The peak is the
+    # FP32 multiply-add rate measured on this GPU by the library's
+    # microbenchmark.  Algorithmic work per face: FLOPS_PER_FACE (the method's
+    # count), FLOPS_PER_FACE_COUNTED (the kernel's own operations) beside it;
+    # bytes per cell: read U^n (4 x 8 B) and L_x (4 x 4 B), write U1 (4 x 8 B).
     peaks, peak_kind = measured_peaks()
+    fma = measure_peaks(local)
     dom = 1
     t_dom = k_ms32[dom] / 1e3
-    props = torch.cuda.get_device_properties(local)
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     flops = FLOPS_PER_FACE * cells
     achieved = flops / t_dom / 1e12
+    achieved_counted = FLOPS_PER_FACE_COUNTED * cells / t_dom / 1e12
     traffic = profiled_traffic("sweep_y_fp32_euler2d.md")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fma["fp32"], "unit": "TFLOP/s",
+                "frac": achieved / fma["fp32"], "traffic": traffic,
                 "kernel": "sweep_kernel<4,5,float> y axis (stage 0, adds L_x, combines)",
-                "peak_kind": "FP32 lanes x clock (%d SMs x 128 x 2 flop x %.0f MHz)"
-                             % (props.multi_processor_count, sm_mhz),
+                "peak_kind": "measured: FP32 multiply-add microbenchmark on this GPU "
+                             "(enoao_measure_fma_peak), 'of measured'",
+                "peak_clock_mhz": fma["clocks"].get("sm_mhz"),
+                "flops_per_face": FLOPS_PER_FACE,
                 "kernel_ms": k_ms32[dom], "algorithmic_flops_per_launch": flops,
+                "counted": {"flops_per_face": FLOPS_PER_FACE_COUNTED,
+                            "achieved": achieved_counted, "frac": achieved_counted / fma["fp32"]},
+                "measured_peaks_tflops": {k: fma[k] for k in ("fp32", "fp32x2", "fp64")},
                 "hbm": {"achieved": BYTES_PER_CELL_Y * cells / t_dom / 1e9,
                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": BYTES_PER_CELL_Y * cells / t_dom / 1e9 / peaks["hbm_gbs"],
                         "algorithmic_bytes_per_launch": BYTES_PER_CELL_Y * cells,
                         "peak_kind": peak_kind}}
+    # the FP64 path's y sweep against the measured FP64 multiply-add rate
+    a64 = flops / (k_ms64[dom] / 1e3) / 1e12
+    roofline64 = {"bound": "fp64 alu", "achieved": a64, "peak": fma["fp64"], "unit": "TFLOP/s",
+                  "frac": a64 / fma["fp64"], "kernel_ms": k_ms64[dom],
+                  "peak_kind": "measured: FP64 multiply-add microbenchmark on this GPU"}
 
     launches = (s32.launches_per_step() * args.steps) if rank == 0 else 0
 
     cpu = None
+    agreement = None
     if rank == 0 and not args.no_cpu:
         rate, sec, threads = cpu_sample(U0, args.cpu_sub)
+        rate1, sec1, _ = cpu_sample(U0, args.cpu_sub1, nthreads=1)
         cpu = {"value": rate, "unit": "cell-stage updates/s", "cores": threads, "kind": "oracle",
+               "cpu_model": cpu_model(),
                "sample": f"one RK3 step of a {args.cpu_sub}x{args.cpu_sub} block of the "
-                         f"4096^2 workload ({sec:.1f} s)"}
+                         f"4096^2 workload ({sec:.1f} s, {threads} threads)",
+               "single_thread": {"value": rate1, "unit": "cell-stage updates/s", "cores": 1,
+                                 "sample": f"one RK3 step of a {args.cpu_sub1}x{args.cpu_sub1} "
+                                           f"block ({sec1:.1f} s)"}}
+        agreement = choice_agreement(evolved64, args.agree_sub, kcmp)
 
     if rank == 0:
         line = {
@@ -338,12 +400,13 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (537 MB state per array)",
                        "tiles": {d: s32.get_tiles(d) for d in range(2)}},
             "fp64": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
-                     "kernel_ms": k_ms64},
+                     "kernel_ms": k_ms64, "clocks": clocks64, "roofline": roofline64},
             "fp32_bulk_speedup_vs_fp64": value / value64,
             "l1_rel_fp32_bulk_vs_fp64": l1, "linf_rel_fp32_bulk_vs_fp64": linf,
             "compare_steps": kcmp, "fp64_fallback_rate": fallback_rate,
             "kernel_ms_fp32_bulk": k_ms32,
             "roofline": roofline, "cpu_baseline": cpu,
+            "fp64_choice_agreement_vs_oracle": agreement,
             "e2e": {"value": e2e_value, "unit": "cell-stage updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches, "clocks": clocks,
@@ -354,6 +417,39 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def choice_agreement(U, sub, steps):
+    """Stencil choices of the FP64 GPU path against the oracle's on a sub x sub
+    block of the evolved workload state (both axes, every field, sign and
+    face): the agreement rate, and how many disagreements the near-tie rule
+    excuses (the oracle's deciding comparison within 1e-13 of the indicators'
+    magnitude) or not."""
+    import oracle
+    import paper_2108_12742_gb300 as eno
+    if U is None:
+        return None
+    n = U.shape[-1]
+    y0 = x0 = (n - sub) // 2  # centre block: the quadrant split runs through it
+    blk = np.ascontiguousarray(U[:, :, y0:y0 + sub, x0:x0 + sub])
+    h = sub / n
+    P = oracle.make_problem((sub, sub), (0.0, 0.0), (h, h), system=oracle.EULER, order=5,
+                            bc=oracle.TRANSMISSIVE)
+    total = agree = excused = 0
+    with eno.Solver((sub, sub), (0.0, 0.0), (h, h), system=eno.EULER, order=5,
+                    bc=eno.TRANSMISSIVE, precision=eno.FP64) as s:
+        s.init_state(blk)
+        for d in range(2):
+            _, idx = s.reconstruct_fluxes(d, want_idx=True)
+            _, io, gap = oracle.fluxes(P, blk, d, want_idx=True)
+            differ = idx != io
+            total += idx.size
+            agree += int((~differ).sum())
+            excused += int((differ & (gap <= 1e-13)).sum())
+    return {"choices": total, "agreement": agree / total, "disagreements": total - agree,
+            "excused_near_ties": excused, "unexcused": total - agree - excused,
+            "sample": f"{sub}x{sub} centre block of the 4096^2 state after {steps} FP64 steps, "
+                      "both axes, every field, sign and face"}
 
 
 # ----------------------------------------------------------------------------
@@ -387,6 +483,8 @@ def run_batched(args):
     import torch
     import paper_2108_12742_gb300 as eno
     from paper_2108_12742_gb300 import inputs
+    clk = ClockSampler(0)
+    clk.start()
     nprob, nsteps = 4096, args.batch_steps
     sizes = inputs.batch_sizes(nprob, seed=2024)
     U = inputs.batch_states(sizes, seed=10_000)
@@ -424,9 +522,10 @@ def run_batched(args):
     per_problem = cells_sub * 3 * nsteps / (ms_sub / 1e3)
     a, b = res["fp32_bulk"]["state"], res["fp64"]["state"]
     l1 = [float(np.abs(a[v] - b[v]).mean() / np.abs(b[v]).mean()) for v in range(3)]
+    clocks = clk.stop()
     _line("batched-euler1d-4096-problems-N256-16384-ao5", res["fp32_bulk"]["value"],
           res["fp32_bulk"]["ms_total"] / nsteps, nsteps, 1,
-          {"config": {"workload": "batched-euler1d-4096-problems-N256-16384-ao5", "cells": cells,
+          {"clocks": clocks, "config": {"workload": "batched-euler1d-4096-problems-N256-16384-ao5", "cells": cells,
                       "problems": nprob, "steps_per_launch": nsteps, "launches": 1},
            "fp64": {"value": res["fp64"]["value"], "ms_total": res["fp64"]["ms_total"]},
            "fp32_bulk_speedup_vs_fp64": res["fp32_bulk"]["value"] / res["fp64"]["value"],
@@ -442,6 +541,8 @@ def run_euler3d(args):
     import torch
     import paper_2108_12742_gb300 as eno
     from paper_2108_12742_gb300 import inputs
+    clk = ClockSampler(0)
+    clk.start()
     n = args.n3d
     U = torch.from_numpy(inputs.euler3d_blast(n, seed=1)).cuda()
     cells = n ** 3
@@ -464,9 +565,10 @@ def run_euler3d(args):
     diff = (states["fp32_bulk"] - states["fp64"]).abs()
     l1 = [float(diff[v].mean() / states["fp64"][v].abs().mean()) for v in range(5)]
     linf = [float(diff[v].max() / states["fp64"][v].abs().max()) for v in range(5)]
+    clocks = clk.stop()
     _line(f"euler3d-{n}^3-periodic-blast-ao7", out["fp32_bulk"]["value"],
           out["fp32_bulk"]["ms_per_step"], out["fp32_bulk"]["steps"], 1,
-          {"config": {"workload": f"euler3d-{n}^3-periodic-blast-ao7", "cells": cells, "order": 7},
+          {"clocks": clocks, "config": {"workload": f"euler3d-{n}^3-periodic-blast-ao7", "cells": cells, "order": 7},
            "fp64": out["fp64"], "kernel_ms_fp32_bulk": out["fp32_bulk"]["kernel_ms"],
            "fp32_bulk_speedup_vs_fp64": out["fp32_bulk"]["value"] / out["fp64"]["value"],
            "l1_rel_fp32_bulk_vs_fp64_one_step": l1, "linf_rel_fp32_bulk_vs_fp64_one_step": linf})
@@ -474,33 +576,133 @@ def run_euler3d(args):
 
 def run_small(args, workload):
     """Launch-bound single problems run to their end time: the 1D Euler Riemann
-    workload (N = 2000, t_end = 0.2) and the periodic advection (N = 200, t = 2)."""
+    workload (N = 2000, t_end = 0.2) and the periodic advection (N = 200, t = 2,
+    the sine and the seeded square pulse), FP32 bulk and FP64, with the
+    FP32-bulk state's L1 / Linf difference from the FP64 one at t_end."""
     import torch
     import paper_2108_12742_gb300 as eno
     from paper_2108_12742_gb300 import inputs
     if workload == "euler1d":
         n, t_end, kw = 2000, 0.2, dict(system=eno.EULER, order=5, bc=eno.TRANSMISSIVE)
-        U, lo, hi = inputs.euler1d_riemann(n, seed=1), 0.0, 1.0
+        runs = [("riemann-seed1", inputs.euler1d_riemann(n, seed=1))]
+        lo, hi = 0.0, 1.0
         name = "euler1d-2000-riemann-ao5-to-t0.2"
     else:
         n, t_end, kw = 200, 2.0, dict(system=eno.SCALAR_ADVECTION, order=5, bc=eno.PERIODIC)
-        U, lo, hi = inputs.advection_sine(n), -1.0, 1.0
-        name = "advection1d-200-sine-ao5-to-t2"
-    out = {}
-    for pname, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
-        with eno.Solver((n,), (lo,), (hi,), precision=prec, **kw) as s:
-            s.init_state(U)
-            s.advance(t_end, cfl=CFL)       # warm-up run (graph capture)
-            s.init_state(U)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            t, k = s.advance(t_end, cfl=CFL)
-            sec = time.perf_counter() - t0
-            out[pname] = {"value": n * 3 * k / sec, "steps": k, "seconds": sec, "t": t}
-    _line(name, out["fp32_bulk"]["value"], 1e3 * out["fp32_bulk"]["seconds"] / out["fp32_bulk"]["steps"],
-          out["fp32_bulk"]["steps"], 1,
-          {"config": {"workload": name, "cells": n},
-           "fp64": out["fp64"], "note": "launch-bound: whole run timed on the host clock"})
+        runs = [("sine", inputs.advection_sine(n)), ("square-seed1", inputs.advection_square(n, 1))]
+        lo, hi = -1.0, 1.0
+        name = "advection1d-200-sine-and-square-ao5-to-t2"
+    clk = ClockSampler(0)
+    clk.start()
+    results = {}
+    for ic, U in runs:
+        out, states = {}, {}
+        for pname, prec in (("fp32_bulk", eno.FP32_BULK), ("fp64", eno.FP64)):
+            with eno.Solver((n,), (lo,), (hi,), precision=prec, **kw) as s:
+                s.init_state(U)
+                s.advance(t_end, cfl=CFL)       # warm-up run (graph capture)
+                s.init_state(U)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                t, k = s.advance(t_end, cfl=CFL)
+                sec = time.perf_counter() - t0
+                states[pname] = s.get_state()
+                out[pname] = {"value": n * 3 * k / sec, "steps": k, "seconds": sec, "t": t}
+        a, b = states["fp32_bulk"], states["fp64"]
+        nv = a.shape[0]
+        out["l1_rel_fp32_bulk_vs_fp64"] = [float(np.abs(a[v] - b[v]).mean() / np.abs(b[v]).mean())
+                                           for v in range(nv)]
+        out["linf_rel_fp32_bulk_vs_fp64"] = [float(np.abs(a[v] - b[v]).max() / np.abs(b[v]).max())
+                                             for v in range(nv)]
+        results[ic] = out
+    clocks = clk.stop()
+    first = results[runs[0][0]]
+    _line(name, first["fp32_bulk"]["value"],
+          1e3 * first["fp32_bulk"]["seconds"] / first["fp32_bulk"]["steps"],
+          first["fp32_bulk"]["steps"], 1,
+          {"config": {"workload": name, "cells": n, "cfl": CFL},
+           "runs": results, "clocks": clocks,
+           "note": "launch-bound: whole run timed on the host clock; value: first run, FP32 bulk"})
+
+
+def run_convergence(args):
+    """The Sec. 4.1 convergence workload on the GPU: u_t + u_x = 0 on [-1, 1],
+    periodic, u0 = sin(pi x), t = 2, errors against the exact solution at
+    N = 25, 50, 100, 200, 400, FP64: ENO-AO5 at CFL 0.5 (third-order
+    Runge-Kutta error dominates: expected order 3) and at dt = dx^(5/3)
+    (designed order 5), ENO-AO7 at dt = dx^(7/3) (designed order 7); the
+    observed orders log2(e(N) / e(2N))."""
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    ns = [25, 50, 100, 200, 400]
+    clk = ClockSampler(0)
+    clk.start()
+    t0 = time.perf_counter()
+    cases = {}
+    for label, order, dtexp in (("ao5-cfl0.5", 5, None), ("ao5-dt-dx^(5/3)", 5, 5 / 3),
+                                ("ao7-dt-dx^(7/3)", 7, 7 / 3)):
+        rows = []
+        for n in ns:
+            U0 = inputs.advection_sine(n)
+            dx = 2.0 / n
+            with eno.Solver((n,), (-1.0,), (1.0,), system=eno.SCALAR_ADVECTION, order=order,
+                            bc=eno.PERIODIC) as s:
+                s.init_state(U0)
+                if dtexp is None:
+                    t, k = s.advance(2.0, cfl=CFL)
+                else:
+                    t, k = s.advance(2.0, dt_fixed=dx ** dtexp)
+                e = np.abs(s.get_state() - U0)   # the exact solution at t = 2 is u0
+            rows.append({"n": n, "steps": k, "l1": float(e.mean()), "linf": float(e.max())})
+        for i in range(1, len(rows)):
+            rows[i]["order_l1"] = float(np.log2(rows[i - 1]["l1"] / rows[i]["l1"]))
+            rows[i]["order_linf"] = float(np.log2(rows[i - 1]["linf"] / rows[i]["linf"]))
+        cases[label] = rows
+    sec = time.perf_counter() - t0
+    clocks = clk.stop()
+    cells_steps = sum(r["n"] * r["steps"] for rows in cases.values() for r in rows)
+    _line("convergence-advection1d-sine-n25-400", cells_steps * 3 / sec, 1e3 * sec, 1, 0,
+          {"config": {"workload": "convergence-advection1d-sine-n25-400", "dtype": "f64"},
+           "dtype": "f64", "convergence": cases, "clocks": clocks,
+           "note": "value: cell-stage updates per host second over all runs (launch-bound)"})
+
+
+def run_sweep_profile(args):
+    """One sweep kernel of a chosen workload, for profiler captures: builds the
+    2D four-quadrant data (the benchmark's, at n x n; --ndim 3 the 3D blast at
+    n^3; --case riemann2 the 2D Riemann configuration 2 on [-1, 1]^2), takes
+    --steps-before steps, sets the tiles and re-decision mode and launches the
+    sweep of axis --dir nrep times (enoao_time_sweep), printing the mean."""
+    import paper_2108_12742_gb300 as eno
+    from paper_2108_12742_gb300 import inputs
+    n = args.prof_n
+    prec = eno.FP32_BULK if args.prof_precision == "fp32" else eno.FP64
+    if args.prof_case == "riemann2":
+        U = inputs.riemann2d(2, n, n)
+        s = eno.Solver((n, n), (-1.0, -1.0), (1.0, 1.0), system=eno.EULER, order=args.prof_order,
+                       bc=eno.TRANSMISSIVE, precision=prec)
+    elif args.prof_ndim == 2:
+        U = inputs.euler2d_quadrants(n, n, seed=1)
+        s = eno.Solver((n, n), (0.0, 0.0), (1.0, 1.0), system=eno.EULER, order=args.prof_order,
+                       bc=eno.TRANSMISSIVE, precision=prec)
+    else:
+        U = inputs.euler3d_blast(n, seed=1)
+        s = eno.Solver((n, n, n), (0.0,) * 3, (1.0,) * 3, system=eno.EULER, order=args.prof_order,
+                       bc=eno.PERIODIC, precision=prec)
+    with s:
+        s.set_redecide(eno.REDECIDE_GRID if args.prof_redecide == "grid" else eno.REDECIDE_IN_SWEEP)
+        s.init_state(U)
+        if args.steps_before:
+            s.advance_steps(args.steps_before, CFL)
+        if args.prof_ta or args.prof_ts:
+            s.set_tiles(args.prof_dir, args.prof_ta, args.prof_ts)
+        f0 = s.stats().fp64_fallbacks
+        ms = s.time_sweep(args.prof_dir, args.prof_nrep)
+        f1 = s.stats().fp64_fallbacks
+        print(f"sweep axis {args.prof_dir} {args.prof_precision} n={n} "
+              f"tiles={s.get_tiles(args.prof_dir)}: {ms:.4f} ms per launch, "
+              f"{(f1 - f0) / (args.prof_nrep + 1):.0f} FP64 re-decisions per launch")
+    return 0
 
 
 def run_paper_cases(args):
@@ -514,6 +716,8 @@ def run_paper_cases(args):
     import torch
     import paper_2108_12742_gb300 as eno
     from paper_2108_12742_gb300 import inputs
+    clk = ClockSampler(0)
+    clk.start()
     n2 = args.paper_n2d
     cases = [
         ("composite-wave", inputs.composite_wave(400), (400,), (-1.0,), (1.0,),
@@ -566,8 +770,9 @@ def run_paper_cases(args):
             rows.append(row)
             total_cs += cells * 3 * res["fp32_bulk"][1]
             total_s += res["fp32_bulk"][2]
+    clocks = clk.stop()
     _line(f"paper-cases-riemann2d-{n2}", total_cs / total_s, 1e3 * total_s, len(rows), 1,
-          {"config": {"workload": f"paper-cases (Sec. 4), 2D at {n2}x{n2}"}, "cases": rows,
+          {"clocks": clocks, "config": {"workload": f"paper-cases (Sec. 4), 2D at {n2}x{n2}"}, "cases": rows,
            "note": "value: all FP32-bulk runs together, cell-stage updates per host second"})
 
 
@@ -580,6 +785,8 @@ def run_adr(args):
     import torch
     import paper_2108_12742_gb300 as eno
     from paper_2108_12742_gb300 import adr
+    clk = ClockSampler(0)
+    clk.start()
     n = args.adr_n
     out = {}
     for order in (5, 7):
@@ -601,8 +808,9 @@ def run_adr(args):
     d7 = float(np.abs(out["ao7_fp32_bulk"]["kappa"] - out["ao7_fp64"]["kappa"]).max())
     for v in out.values():
         del v["kappa"]
+    clocks = clk.stop()
     _line(f"adr-{n}-modes", out["ao5_fp64"]["modes_per_s"], 1e3 * out["ao5_fp64"]["seconds"], 1, 1,
-          {"config": {"workload": f"ADR of ENO-AO5/AO7, {n // 2} cosine modes of amplitude 1 on "
+          {"clocks": clocks, "config": {"workload": f"ADR of ENO-AO5/AO7, {n // 2} cosine modes of amplitude 1 on "
                                   f"{n} periodic cells, one sweep"},
            "unit": "modes/s", "dtype": "f64",
            "unit_note": "value: ENO-AO5 FP64 modes per host second, end to end",
@@ -617,6 +825,8 @@ def run_tie_study(args):
     import torch
     import paper_2108_12742_gb300 as eno
     from paper_2108_12742_gb300 import inputs
+    clk = ClockSampler(0)
+    clk.start()
     n, before = args.tie_n, args.tie_evolve
     U = inputs.euler2d_quadrants(n, n, seed=1)
     kw = dict(system=eno.EULER, order=5)
@@ -651,9 +861,10 @@ def run_tie_study(args):
                      "redecided_per_step": (f3 - f2) / args.steps, "ms_per_step": ms})
     best = min(rows, key=lambda r: r["ms_per_step"])
     cells = n * n
+    clocks = clk.stop()
     _line(f"tie-study-euler2d-{n}x{n}-evolved{before}", cells * 3 / (best["ms_per_step"] * 1e-3),
           best["ms_per_step"], args.steps, 2,
-          {"config": {"workload": f"tie-study-euler2d-{n}x{n}-evolved{before}", "order": 5},
+          {"clocks": clocks, "config": {"workload": f"tie-study-euler2d-{n}x{n}-evolved{before}", "order": 5},
            "tie_study": rows,
            "note": "value: fastest tie_rel; agreement against the FP64 path on the same state"})
 
@@ -666,11 +877,25 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--cpu-sub", type=int, default=1536)
+    ap.add_argument("--cpu-sub1", type=int, default=512)
+    ap.add_argument("--agree-sub", type=int, default=384)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default="euler2d",
                     choices=["euler2d", "batched", "euler3d", "euler1d", "advection",
-                             "tie-study", "paper-cases", "adr"])
+                             "tie-study", "paper-cases", "adr", "convergence", "sweep"])
+    # --workload sweep: one sweep kernel (profiler captures)
+    ap.add_argument("--prof-n", type=int, default=2048)
+    ap.add_argument("--prof-ndim", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--prof-order", type=int, default=5)
+    ap.add_argument("--prof-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prof-dir", type=int, default=0)
+    ap.add_argument("--prof-nrep", type=int, default=2)
+    ap.add_argument("--prof-ta", type=int, default=0)
+    ap.add_argument("--prof-ts", type=int, default=0)
+    ap.add_argument("--prof-case", default="quadrants", choices=["quadrants", "riemann2"])
+    ap.add_argument("--prof-redecide", default="in_sweep", choices=["in_sweep", "grid"])
+    ap.add_argument("--steps-before", type=int, default=0)
     ap.add_argument("--adr-n", type=int, default=4096)
     ap.add_argument("--paper-n2d", type=int, default=800)
     ap.add_argument("--tie-n", type=int, default=2048)
@@ -694,6 +919,10 @@ def main():
         return run_adr(args)
     if args.workload == "paper-cases":
         return run_paper_cases(args)
+    if args.workload == "convergence":
+        return run_convergence(args)
+    if args.workload == "sweep":
+        return run_sweep_profile(args)
     return run_gpu(args)
 
 
