@@ -121,6 +121,13 @@ enoao_status enoao_batch_create(const enoao_config *proto, int nprob, const int6
                                 const double *lo, const double *hi, void *cuda_stream,
                                 enoao_ctx **out);
 
+/* Time reached, the Lax-Friedrichs alpha its last step split with (Sec. 2:
+ * the maximum of |f'(u)| over that problem's mesh) and the last step size of
+ * problem p of a batched context (synchronises).  Null outputs are skipped.
+ * ENOAO_EINVAL for a context that is not batched or p outside 0..nprob-1. */
+enoao_status enoao_batch_problem_stats(enoao_ctx *ctx, int p, double *t, double *alpha,
+                                       double *dt);
+
 /* Releases every resource of the context (NULL is ignored). */
 void enoao_destroy(enoao_ctx *ctx);
 

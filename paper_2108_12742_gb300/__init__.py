@@ -83,6 +83,7 @@ def load():
         "enoao_batch_create": (ctypes.c_int, [C, ctypes.c_int, ctypes.POINTER(I64), D, D, P,
                                               ctypes.POINTER(P)]),
         "enoao_destroy": (None, [P]),
+        "enoao_batch_problem_stats": (ctypes.c_int, [P, ctypes.c_int, D, D, D]),
         "enoao_last_error": (ctypes.c_char_p, [P]),
         "enoao_init_state": (ctypes.c_int, [P, P, ctypes.c_int]),
         "enoao_get_state": (ctypes.c_int, [P, P, ctypes.c_int]),
@@ -356,3 +357,10 @@ class Batch(Solver):
             lo.ctypes.data_as(D), hi.ctypes.data_as(D), _stream_handle(stream), ctypes.byref(self._h))
         if st:
             raise EnoaoError(st, self._lib.enoao_last_error(None).decode())
+
+    def problem_stats(self, p):
+        """(t, alpha of the last step, last dt) of problem p."""
+        t, a, dt = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.enoao_batch_problem_stats(self._h, p, ctypes.byref(t),
+                                                        ctypes.byref(a), ctypes.byref(dt)))
+        return t.value, a.value, dt.value

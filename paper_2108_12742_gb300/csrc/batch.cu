@@ -123,7 +123,9 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
     }
     double t = B.t[p], dt = 0.0;
     const bool per_stage = NV > 1 && B.per_stage_alpha;
+    double alpha_step = alpha;  // alpha the last step split with
     for (int step = 0; step < B.nsteps; ++step) {
+      alpha_step = alpha;
       dt = B.cfl / (alpha / dx);
       double a_stage = alpha;  // splitting constant of the current stage
       for (int stage = 0; stage < 3; ++stage) {
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
     }
     if (threadIdx.x == 0) {
       B.t[p] = t;
-      B.alpha[p] = alpha;
+      B.alpha[p] = alpha_step;
       B.dt[p] = dt;
     }
   }
@@ -454,6 +456,35 @@ enoao_status batch_stats(enoao_ctx* c, enoao_stats* out) {
   out->fp64_fallbacks = c->st_host->fallbacks;
   return ENOAO_OK;
 }
+
+}  // namespace enoao
+
+extern "C" enoao_status enoao_batch_problem_stats(enoao_ctx* c, int p, double* t, double* alpha,
+                                                  double* dt) {
+  using namespace enoao;
+  if (!c) return ENOAO_EINVAL;
+  if (!c->batch) {
+    c->err = "not a batched context";
+    return ENOAO_EINVAL;
+  }
+  BatchState* b = c->batch;
+  if (p < 0 || p >= b->nprob) {
+    c->err = "problem index out of range";
+    return ENOAO_EINVAL;
+  }
+  enoao_status r = read_err(c);
+  if (r != ENOAO_OK && r != ENOAO_ENONPHYS) return r;
+  double v[3] = {0.0, 0.0, 0.0};
+  BCU(c, cudaMemcpy(&v[0], b->t + p, sizeof(double), cudaMemcpyDeviceToHost));
+  BCU(c, cudaMemcpy(&v[1], b->alpha + p, sizeof(double), cudaMemcpyDeviceToHost));
+  BCU(c, cudaMemcpy(&v[2], b->dt + p, sizeof(double), cudaMemcpyDeviceToHost));
+  if (t) *t = v[0];
+  if (alpha) *alpha = v[1];
+  if (dt) *dt = v[2];
+  return ENOAO_OK;
+}
+
+namespace enoao {
 
 // Times one step of the whole batch for each (tile, block) candidate on a
 // saved copy of the state and keeps the fastest.
