@@ -121,6 +121,61 @@ enoao_status enoao_batch_create(const enoao_config *proto, int nprob, const int6
                                 const double *lo, const double *hi, void *cuda_stream,
                                 enoao_ctx **out);
 
+/* ---- Domain decomposition: a sub-domain of a grid split along its last axis.
+ * The conservation form (Sec. 2, Eq. 1DWENOFD) needs, per Runge-Kutta stage,
+ * the G = order/2 + 2 cells beyond a cell on each side of every axis, and
+ * alpha of the global splitting is the maximum of |f'(u)| over the whole mesh
+ * (Sec. 2).  A sub-domain context owns the layers [offset, offset + n_local)
+ * of the last axis of the global problem (2D: rows, 3D: planes) and keeps G
+ * ghost layers on each side of that axis in its arrays.  A step is then:
+ * alpha = max over sub-domains of enoao_local_alpha, enoao_set_step_alpha,
+ * dt = cfl / sum_d alpha_d / dx_d, and per stage k = 0, 1, 2: fill the ghost
+ * layers of stage state k (enoao_halo_export on the neighbour, exchange,
+ * enoao_halo_import here; enoao_halo_fill_transmissive at a transmissive edge
+ * of the global grid; a periodic edge exchanges with the sub-domain at the
+ * other end), then enoao_rk_stage(ctx, k, dt).  Results equal the undivided
+ * grid's bit for bit.  enoao_init_state / enoao_get_state /
+ * enoao_get_stage_state take the sub-domain's interior ([nv][n_local layers]);
+ * non-physical cells are reported by their interior index.
+ *
+ * Creates the context of layers [offset, offset + n_local) of the 2D or 3D
+ * problem global (its n, lo, hi, bc and constants).  Errors: as
+ * enoao_create; ENOAO_EINVAL for a 1D problem, alpha_mode other than
+ * ENOAO_ALPHA_PER_STEP, n_local < G or a range outside the grid.  Sub-domains
+ * step stage by stage only (enoao_advance* return ENOAO_EINVAL) and FP32 bulk
+ * re-decides its near-ties inside the sweep. */
+enoao_status enoao_create_subdomain(const enoao_config *global, int64_t offset, int64_t n_local,
+                                    void *cuda_stream, enoao_ctx **out);
+
+/* Halo layers of stage state k (0: U^n, 1: U^(1), 2: U^(2)) on side 0 (low
+ * index) or 1 (high index) of the split axis.  The buffer holds
+ * [nv][G][plane] doubles, layers in increasing index order, plane the cells
+ * of one layer (2D: n[0], 3D: n[0] n[1]).  Export copies the G interior
+ * layers next to the side out; import writes the G ghost layers beyond it.
+ * Both synchronise.  ENOAO_EINVAL for a context that is not a sub-domain, k
+ * outside 0..2 or side not 0 or 1. */
+enoao_status enoao_halo_export(enoao_ctx *ctx, int k, int side, double *buf, int on_device);
+enoao_status enoao_halo_import(enoao_ctx *ctx, int k, int side, const double *buf,
+                               int on_device);
+
+/* Zero-gradient ghost layers (the transmissive boundary, each ghost layer a
+ * copy of the edge layer) beyond side of stage state k; for a sub-domain at
+ * a transmissive edge of the global grid.  Synchronises. */
+enoao_status enoao_halo_fill_transmissive(enoao_ctx *ctx, int k, int side);
+
+/* The maximum over this context's cells of the Lax-Friedrichs alpha per axis
+ * (Sec. 2: |u_d| + c for the Euler equations, |a| for advection) for the
+ * current U^n, in the arithmetic of the context's precision; for a
+ * sub-domain, the value to take the maximum over all sub-domains of.
+ * Synchronises; ENOAO_ENONPHYS if U^n holds a non-physical cell. */
+enoao_status enoao_local_alpha(enoao_ctx *ctx, double *alpha);
+
+/* Sets the alpha per axis that the next step (enoao_rk_stage stage 0) splits
+ * with, in place of this context's own maximum -- the global maximum of a
+ * decomposed grid.  ENOAO_EINVAL for negative or non-finite values, batched
+ * contexts and alpha modes other than ENOAO_ALPHA_PER_STEP. */
+enoao_status enoao_set_step_alpha(enoao_ctx *ctx, const double *alpha);
+
 /* Time reached, the Lax-Friedrichs alpha its last step split with (Sec. 2:
  * the maximum of |f'(u)| over that problem's mesh) and the last step size of
  * problem p of a batched context (synchronises).  Null outputs are skipped.

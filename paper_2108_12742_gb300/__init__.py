@@ -84,6 +84,12 @@ def load():
                                               ctypes.POINTER(P)]),
         "enoao_destroy": (None, [P]),
         "enoao_batch_problem_stats": (ctypes.c_int, [P, ctypes.c_int, D, D, D]),
+        "enoao_create_subdomain": (ctypes.c_int, [C, I64, I64, P, ctypes.POINTER(P)]),
+        "enoao_halo_export": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]),
+        "enoao_halo_import": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int]),
+        "enoao_halo_fill_transmissive": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int]),
+        "enoao_local_alpha": (ctypes.c_int, [P, D]),
+        "enoao_set_step_alpha": (ctypes.c_int, [P, D]),
         "enoao_last_error": (ctypes.c_char_p, [P]),
         "enoao_init_state": (ctypes.c_int, [P, P, ctypes.c_int]),
         "enoao_get_state": (ctypes.c_int, [P, P, ctypes.c_int]),
@@ -336,6 +342,56 @@ class Solver:
 
     def autotune(self):
         self._check(self._lib.enoao_autotune(self._h))
+
+
+class SubDomain(Solver):
+    """Layers [offset, offset + n_local) of the last axis of a 2D/3D problem
+    (enoao_create_subdomain); shape, lo, hi describe the global grid."""
+
+    def __init__(self, shape, lo, hi, offset, n_local, stream=None, **kw):
+        self._lib = load()
+        self.cfg = make_config(shape, lo, hi, **kw)
+        self.global_shape = tuple(int(s) for s in shape)
+        local = list(self.global_shape)
+        local[-1] = int(n_local)
+        self.shape = tuple(local)
+        self.offset, self.n_local = int(offset), int(n_local)
+        self.nv = len(shape) + 2 if self.cfg.system == EULER else 1
+        full = list(self.shape) + [1] * (3 - len(self.shape))
+        self.state_shape = (self.nv, full[2], full[1], full[0])
+        self.G = self.cfg.order // 2 + 2
+        self.plane = int(np.prod(self.shape[:-1]))
+        self.halo_shape = (self.nv, self.G, self.plane)
+        self._h = ctypes.c_void_p()
+        st = self._lib.enoao_create_subdomain(ctypes.byref(self.cfg), self.offset, self.n_local,
+                                              _stream_handle(stream), ctypes.byref(self._h))
+        if st:
+            raise EnoaoError(st, self._lib.enoao_last_error(None).decode())
+
+    def halo_export(self, k, side, out=None):
+        if out is None:
+            out = np.empty(self.halo_shape)
+        p, dev = _ptr(out)
+        self._check(self._lib.enoao_halo_export(self._h, k, side, p, dev))
+        return out
+
+    def halo_import(self, k, side, buf):
+        p, dev = _ptr(buf)
+        self._check(self._lib.enoao_halo_import(self._h, k, side, p, dev))
+
+    def halo_fill_transmissive(self, k, side):
+        self._check(self._lib.enoao_halo_fill_transmissive(self._h, k, side))
+
+    def local_alpha(self):
+        a = np.zeros(3)
+        self._check(self._lib.enoao_local_alpha(self._h, a.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_double))))
+        return a
+
+    def set_step_alpha(self, alpha):
+        a = np.ascontiguousarray(alpha, dtype=np.float64)
+        self._check(self._lib.enoao_set_step_alpha(self._h, a.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_double))))
 
 
 class Batch(Solver):

@@ -65,8 +65,8 @@ constexpr double kInf = std::numeric_limits<double>::infinity();
 // (speeds32), so that a step from a state set here takes the same alpha as
 // the uninterrupted run did.
 template <int NV, bool BULK, bool FIELD>
-__global__ void alpha_kernel(const double* __restrict__ U, long long ncell, double gamma,
-                             StepState* st, int slot) {
+__global__ void alpha_kernel(const double* __restrict__ U, long long ncell, long long cstride,
+                             double gamma, StepState* st, int slot) {
   constexpr int ND = NV - 2;
   double amax[3] = {0, 0, 0};
   double af[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -74,7 +74,7 @@ __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, doub
        i += (long long)gridDim.x * blockDim.x) {
     double u[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) u[c] = U[c * ncell + i];
+    for (int c = 0; c < NV; ++c) u[c] = U[c * cstride + i];
     double s[3];
     const bool ok = BULK ? speeds32<NV, false>(u, gamma, s) : speeds64<NV, false>(u, gamma, s);
     if (!ok) {
@@ -118,27 +118,28 @@ __global__ void alpha_kernel(const double* __restrict__ U, long long ncell, doub
 }
 
 template <int NV>
-void launch_alpha_nv(const double* U, long long ncell, double gamma, StepState* st, int slot,
-                     bool bulk, bool field, int blocks, cudaStream_t s) {
+void launch_alpha_nv(const double* U, long long ncell, long long cstride, double gamma,
+                     StepState* st, int slot, bool bulk, bool field, int blocks, cudaStream_t s) {
   if (bulk) {
     if (field)
-      alpha_kernel<NV, true, true><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+      alpha_kernel<NV, true, true><<<blocks, 256, 0, s>>>(U, ncell, cstride, gamma, st, slot);
     else
-      alpha_kernel<NV, true, false><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+      alpha_kernel<NV, true, false><<<blocks, 256, 0, s>>>(U, ncell, cstride, gamma, st, slot);
   } else {
     if (field)
-      alpha_kernel<NV, false, true><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+      alpha_kernel<NV, false, true><<<blocks, 256, 0, s>>>(U, ncell, cstride, gamma, st, slot);
     else
-      alpha_kernel<NV, false, false><<<blocks, 256, 0, s>>>(U, ncell, gamma, st, slot);
+      alpha_kernel<NV, false, false><<<blocks, 256, 0, s>>>(U, ncell, cstride, gamma, st, slot);
   }
 }
 
-// Launches alpha_kernel for an Euler state of nv = 3, 4 or 5 variables.
-void launch_alpha(int nv, const double* U, long long ncell, double gamma, StepState* st, int slot,
-                  bool bulk, bool field, int blocks, cudaStream_t s) {
-  if (nv == 3) launch_alpha_nv<3>(U, ncell, gamma, st, slot, bulk, field, blocks, s);
-  if (nv == 4) launch_alpha_nv<4>(U, ncell, gamma, st, slot, bulk, field, blocks, s);
-  if (nv == 5) launch_alpha_nv<5>(U, ncell, gamma, st, slot, bulk, field, blocks, s);
+// Launches alpha_kernel for an Euler state of nv = 3, 4 or 5 variables: ncell
+// cells from U on, conserved components cstride apart.
+void launch_alpha(int nv, const double* U, long long ncell, long long cstride, double gamma,
+                  StepState* st, int slot, bool bulk, bool field, int blocks, cudaStream_t s) {
+  if (nv == 3) launch_alpha_nv<3>(U, ncell, cstride, gamma, st, slot, bulk, field, blocks, s);
+  if (nv == 4) launch_alpha_nv<4>(U, ncell, cstride, gamma, st, slot, bulk, field, blocks, s);
+  if (nv == 5) launch_alpha_nv<5>(U, ncell, cstride, gamma, st, slot, bulk, field, blocks, s);
 }
 
 struct StepConsts {
@@ -322,7 +323,7 @@ enoao_status check_tiles(enoao_ctx* c, int d, int ta, int ts) {
 // re-decision pass after each sweep instead of being re-decided inside the
 // sweep's tiles (enoao_set_redecide; AUTO currently re-decides in the sweep).
 bool use_list(const enoao_ctx* c) {
-  if (!fp32(c) || c->batch || c->redecide != ENOAO_REDECIDE_GRID) return false;
+  if (!fp32(c) || c->batch || c->sub || c->redecide != ENOAO_REDECIDE_GRID) return false;
   if (consts(c).field) return false;  // per-field splitting re-decides in the sweep
   long long faces = 0;
   for (int d = 0; d < c->cfg.ndim; ++d)
@@ -382,10 +383,11 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
     a.dx_all[k] = c->dx[k];
   }
   a.ncell = c->ncell;
-  a.cstride = c->ncell;
+  a.cstride = c->carr;
+  a.org = c->org;
   a.ndim = c->cfg.ndim;
   a.dir = d;
-  a.bc = c->cfg.bc[d];
+  a.bc = c->sub && d == c->cfg.ndim - 1 ? kBcHalo : c->cfg.bc[d];
   a.mode = mode;
   a.stage = stage;
   a.ta = c->ta[d];
@@ -543,11 +545,20 @@ enoao_status check_err(enoao_ctx* c) {
   return ENOAO_OK;
 }
 
-enoao_status copy_in(enoao_ctx* c, double* dst, const double* src, size_t bytes, int on_device) {
-  CU(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                        c->s));
+// Copies the interior of a state array from (in) or to the caller's buffer
+// ([nv][ncell], contiguous): one 2D copy, component rows carr apart in the array.
+enoao_status copy_interior(enoao_ctx* c, double* arr, const double* user_in, int on_device, bool in) {
+  const size_t w = (size_t)c->ncell * sizeof(double), pitch = (size_t)c->carr * sizeof(double);
+  double* user = const_cast<double*>(user_in);
+  if (in)
+    CU(c, cudaMemcpy2DAsync(arr + c->org, pitch, user, w, w, c->nv,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+  else
+    CU(c, cudaMemcpy2DAsync(user, w, arr + c->org, pitch, w, c->nv,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
   return ENOAO_OK;
 }
+
 
 }  // namespace
 
@@ -615,7 +626,7 @@ static enoao_status validate(const enoao_config* cfg, bool batched) {
 }
 
 static enoao_status create_common(const enoao_config* cfg, void* stream, enoao_ctx** out,
-                                  bool batched) {
+                                  bool batched, long long ghost_layer_cells = 0) {
   enoao_ctx* c = new (std::nothrow) enoao_ctx;
   if (!c) return fail(nullptr, ENOAO_ENOMEM, "host allocation failed");
   c->cfg = *cfg;
@@ -637,11 +648,14 @@ static enoao_status create_common(const enoao_config* cfg, void* stream, enoao_c
   }
   if (!batched) {
     c->ncell = cfg->n[0] * cfg->n[1] * cfg->n[2];
+    // ghost layers of a sub-domain: halo() layers on each side of the split axis
+    c->org = ghost_layer_cells;
+    c->carr = c->ncell + 2 * ghost_layer_cells;
     for (int d = 0; d < 3; ++d) c->dx[d] = d < cfg->ndim ? (cfg->hi[d] - cfg->lo[d]) / cfg->n[d] : 1.0;
-    const size_t bytes = (size_t)c->nv * c->ncell * sizeof(double);
+    const size_t bytes = (size_t)c->nv * c->carr * sizeof(double);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->U[k], bytes);
     if (e == cudaSuccess && cfg->ndim > 1)
-      e = cudaMalloc(&c->rhs, (size_t)c->nv * c->ncell * (fp32(c) ? 4 : 8));
+      e = cudaMalloc(&c->rhs, (size_t)c->nv * c->carr * (fp32(c) ? 4 : 8));
     if (e != cudaSuccess) {
       enoao_status r = fail(nullptr, e == cudaErrorMemoryAllocation ? ENOAO_ENOMEM : ENOAO_ECUDA,
                             "device allocation of %zu bytes per state failed: %s", bytes,
@@ -674,6 +688,139 @@ enoao_status enoao_create(const enoao_config* cfg, void* cuda_stream, enoao_ctx*
   enoao_status r = validate(cfg, false);
   if (r != ENOAO_OK) return r;
   return create_common(cfg, cuda_stream, out, false);
+}
+
+enoao_status enoao_create_subdomain(const enoao_config* global, int64_t offset, int64_t n_local,
+                                    void* cuda_stream, enoao_ctx** out) {
+  if (!out) return fail(nullptr, ENOAO_EINVAL, "out is NULL");
+  *out = nullptr;
+  enoao_status r = validate(global, false);
+  if (r != ENOAO_OK) return r;
+  if (global->ndim < 2)
+    return fail(nullptr, ENOAO_EINVAL, "sub-domains split 2D or 3D grids along their last axis");
+  if (global->alpha_mode != ENOAO_ALPHA_PER_STEP)
+    return fail(nullptr, ENOAO_EINVAL, "sub-domains take one alpha per step (ENOAO_ALPHA_PER_STEP)");
+  const int last = global->ndim - 1, G = halo(global->order);
+  if (offset < 0 || n_local < G || offset + n_local > global->n[last])
+    return fail(nullptr, ENOAO_EINVAL,
+                "layers [%lld, %lld) are not a sub-domain of %lld layers with at least %d of its own",
+                (long long)offset, (long long)(offset + n_local), (long long)global->n[last], G);
+  enoao_config local = *global;
+  local.n[last] = n_local;
+  long long plane = 1;
+  for (int d = 0; d < last; ++d) plane *= global->n[d];
+  enoao_ctx* c = nullptr;
+  r = create_common(&local, cuda_stream, &c, false, G * plane);
+  if (r != ENOAO_OK) return r;
+  c->sub = 1;
+  c->plane = plane;
+  c->sub_off = offset;
+  c->sub_bc = global->bc[last];
+  for (int d = 0; d < global->ndim; ++d)  // the global spacing, bit for bit
+    c->dx[d] = (global->hi[d] - global->lo[d]) / global->n[d];
+  *out = c;
+  return ENOAO_OK;
+}
+
+// Halo layers of a sub-domain: the caller's buffer holds [nv][G][plane]
+// (layers in increasing index order).  Export takes the G interior layers
+// next to side (0: low, 1: high) of stage state k; import writes the G ghost
+// layers beyond that side.
+static enoao_status halo_copy(enoao_ctx* c, int k, int side, double* buf, int on_device, bool out) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (!c->sub) return fail(c, ENOAO_EINVAL, "not a sub-domain context");
+  if (k < 0 || k > 2 || (side != 0 && side != 1) || !buf)
+    return fail(c, ENOAO_EINVAL, "stage state k must be 0..2, side 0 or 1, buffer non-NULL");
+  const int G = halo(c->cfg.order);
+  const long long nl = c->cfg.n[c->cfg.ndim - 1];
+  long long at;  // first array cell of the G layers
+  if (out)
+    at = c->org + (side == 0 ? 0 : (nl - G) * c->plane);
+  else
+    at = side == 0 ? 0 : c->org + nl * c->plane;
+  const size_t w = (size_t)G * c->plane * sizeof(double), pitch = (size_t)c->carr * sizeof(double);
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  if (out)
+    CU(c, cudaMemcpy2DAsync(buf, w, c->U[k] + at, pitch, w, c->nv,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  else
+    CU(c, cudaMemcpy2DAsync(c->U[k] + at, pitch, buf, w, w, c->nv,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+enoao_status enoao_halo_export(enoao_ctx* c, int k, int side, double* buf, int on_device) {
+  return halo_copy(c, k, side, buf, on_device, true);
+}
+
+enoao_status enoao_halo_import(enoao_ctx* c, int k, int side, const double* buf, int on_device) {
+  return halo_copy(c, k, side, const_cast<double*>(buf), on_device, false);
+}
+
+enoao_status enoao_halo_fill_transmissive(enoao_ctx* c, int k, int side) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (!c->sub) return fail(c, ENOAO_EINVAL, "not a sub-domain context");
+  if (k < 0 || k > 2 || (side != 0 && side != 1))
+    return fail(c, ENOAO_EINVAL, "stage state k must be 0..2 and side 0 or 1");
+  const int G = halo(c->cfg.order);
+  const long long nl = c->cfg.n[c->cfg.ndim - 1];
+  // zero-gradient ghosts: every ghost layer is a copy of the edge layer
+  const long long edge = c->org + (side == 0 ? 0 : (nl - 1) * c->plane);
+  const size_t w = (size_t)c->plane * sizeof(double), pitch = (size_t)c->carr * sizeof(double);
+  enoao_status r = enter(c);
+  if (r != ENOAO_OK) return r;
+  for (int g = 0; g < G; ++g) {
+    const long long at = side == 0 ? g * c->plane : c->org + (nl + g) * c->plane;
+    CU(c, cudaMemcpy2DAsync(c->U[k] + at, pitch, c->U[k] + edge, pitch, w, c->nv,
+                            cudaMemcpyDeviceToDevice, c->s));
+  }
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
+}
+
+enoao_status enoao_local_alpha(enoao_ctx* c, double* alpha) {
+  if (!c || !alpha) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  enoao_status r = read_host_state(c);
+  if (r != ENOAO_OK) return r;
+  r = check_err(c);
+  if (r != ENOAO_OK) return r;
+  const int cur = (int)(c->st_host->steps & 1);
+  for (int d = 0; d < 3; ++d)
+    alpha[d] = d < c->cfg.ndim && c->cfg.system == ENOAO_EULER
+                   ? __builtin_bit_cast(double, c->st_host->alpha_acc[cur][d])
+                   : (d < c->cfg.ndim ? std::fabs(c->cfg.adv_speed) : 0.0);
+  return ENOAO_OK;
+}
+
+enoao_status enoao_set_step_alpha(enoao_ctx* c, const double* alpha) {
+  if (!c || !alpha) return fail(c, ENOAO_EINVAL, "NULL argument");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  if (c->cfg.alpha_mode != ENOAO_ALPHA_PER_STEP)
+    return fail(c, ENOAO_EINVAL, "a step alpha can be set with ENOAO_ALPHA_PER_STEP only");
+  for (int d = 0; d < c->cfg.ndim; ++d)
+    if (!(alpha[d] >= 0.0) || !std::isfinite(alpha[d]))
+      return fail(c, ENOAO_EINVAL, "alpha must be finite and >= 0");
+  enoao_status r = read_host_state(c);
+  if (r != ENOAO_OK) return r;
+  const int cur = (int)(c->st_host->steps & 1);
+  unsigned long long bits[3] = {0ull, 0ull, 0ull};
+  for (int d = 0; d < c->cfg.ndim; ++d) bits[d] = __builtin_bit_cast(unsigned long long, alpha[d]);
+  r = enter(c);
+  if (r != ENOAO_OK) return r;
+  std::memcpy(c->st_host->alpha_acc[cur], bits, sizeof bits);  // pinned staging
+  CU(c, cudaMemcpyAsync(&c->st->alpha_acc[cur][0], c->st_host->alpha_acc[cur], sizeof bits,
+                        cudaMemcpyHostToDevice, c->s));
+  r = leave(c);
+  if (r != ENOAO_OK) return r;
+  CU(c, cudaStreamSynchronize(c->s));
+  return ENOAO_OK;
 }
 
 enoao_status enoao_batch_create(const enoao_config* proto, int nprob, const int64_t* n,
@@ -723,13 +870,13 @@ enoao_status enoao_init_state(enoao_ctx* c, const double* U, int on_device) {
   if (c->batch) return batch_init_state(c, U, on_device);
   enoao_status r = enter(c);
   if (r != ENOAO_OK) return r;
-  r = copy_in(c, c->U[0], U, (size_t)c->nv * c->ncell * sizeof(double), on_device);
+  r = copy_interior(c, c->U[0], U, on_device, true);
   if (r != ENOAO_OK) return r;
   reset_state_kernel<<<1, 1, 0, c->s>>>(c->st);
   if (c->cfg.system == ENOAO_EULER) {
     const int blocks = std::max(1, std::min<int>((int)((c->ncell + 255) / 256), c->sms * 8));
-    launch_alpha(c->nv, c->U[0], c->ncell, c->cfg.gamma, c->st, 0, fp32(c), consts(c).field != 0,
-                 blocks, c->s);
+    launch_alpha(c->nv, c->U[0] + c->org, c->ncell, c->carr, c->cfg.gamma, c->st, 0, fp32(c),
+                 consts(c).field != 0, blocks, c->s);
   }
   CU(c, cudaGetLastError());
   r = leave(c);
@@ -744,8 +891,8 @@ enoao_status enoao_get_state(enoao_ctx* c, double* U, int on_device) {
   if (c->batch) return batch_get_state(c, U, on_device);
   enoao_status r = enter(c);
   if (r != ENOAO_OK) return r;
-  CU(c, cudaMemcpyAsync(U, c->U[0], (size_t)c->nv * c->ncell * sizeof(double),
-                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  r = copy_interior(c, c->U[0], U, on_device, false);
+  if (r != ENOAO_OK) return r;
   r = leave(c);
   if (r != ENOAO_OK) return r;
   CU(c, cudaStreamSynchronize(c->s));
@@ -758,8 +905,8 @@ enoao_status enoao_get_stage_state(enoao_ctx* c, int k, double* U, int on_device
   if (k < 0 || k > 2) return fail(c, ENOAO_EINVAL, "stage state k must be 0, 1 or 2");
   enoao_status r = enter(c);
   if (r != ENOAO_OK) return r;
-  CU(c, cudaMemcpyAsync(U, c->U[k], (size_t)c->nv * c->ncell * sizeof(double),
-                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->s));
+  r = copy_interior(c, c->U[k], U, on_device, false);
+  if (r != ENOAO_OK) return r;
   r = leave(c);
   if (r != ENOAO_OK) return r;
   CU(c, cudaStreamSynchronize(c->s));
@@ -831,6 +978,9 @@ enoao_status enoao_rk_stage(enoao_ctx* c, int stage, double dt) {
 
 static enoao_status run_graph_steps(enoao_ctx* c, double t_end, double cfl, double dt_fixed,
                                     long long max_steps, bool until_time, bool sync) {
+  if (c->sub)
+    return fail(c, ENOAO_EINVAL,
+                "a sub-domain steps stage by stage (enoao_rk_stage) between halo exchanges");
   enoao_status r = enter(c);
   if (r != ENOAO_OK) return r;
   r = build_graph(c, steps_per_graph(c));
@@ -1008,7 +1158,7 @@ enoao_status enoao_autotune(enoao_ctx* c) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
   if (c->batch) return batch_autotune(c);
   // Save the state; time one stage-0 sweep per candidate on the live state.
-  const size_t bytes = (size_t)c->nv * c->ncell * sizeof(double);
+  const size_t bytes = (size_t)c->nv * c->carr * sizeof(double);
   enoao_status r = enter(c);
   if (r != ENOAO_OK) return r;
   CU(c, cudaMemcpyAsync(c->U[2], c->U[0], bytes, cudaMemcpyDeviceToDevice, c->s));

@@ -46,4 +46,14 @@ struct enoao_ctx {
   unsigned* redo_mark = nullptr;       // per face
   long long redo_cap = 0;
   int redo_passes = -1;                // in-sweep re-decision pass bound (-1: 64 nv)
+  // Arrays: carr cells per conserved component, the interior from cell org on.
+  // A sub-domain (enoao_create_subdomain) owns layers [sub_off, sub_off + n[last])
+  // of a grid split along its last axis and keeps halo() ghost layers on each
+  // side of that axis in its arrays; otherwise carr = ncell and org = 0.
+  long long carr = 0;
+  long long org = 0;
+  int sub = 0;
+  long long plane = 0;    // cells of one layer across the split axis
+  long long sub_off = 0;  // global index of the first interior layer
+  int sub_bc = 0;         // the global boundary condition along the split axis
 };

@@ -43,6 +43,10 @@ struct StepState {
 };
 
 
+// Ghost cells along the split axis of a sub-domain are layers of the state
+// arrays themselves (filled by halo exchange), read as they are.
+constexpr int kBcHalo = 2;
+
 constexpr int kErrNonPhys = 1;
 constexpr int kErrTimeout = 2;
 constexpr int kErrRedoFull = 4;  // re-decision list full (cannot happen: one slot per face)
@@ -75,9 +79,11 @@ struct SweepArgs {
   long long ncell;      // total cells
   long long nfaces;     // faces of the swept axis, ncell / nd * (nd + 1) (flux output layout)
   long long cstride;    // distance between two conserved components in the state arrays
+  long long org;        // array cell of the first interior cell (sub-domains keep ghost
+                        // layers in their arrays along the split axis; 0 otherwise)
   int ndim;
   int dir;              // swept axis
-  int bc;               // boundary condition along dir
+  int bc;               // boundary condition along dir (kBcHalo: ghosts stored in the arrays)
   int mode;
   int stage;            // Runge-Kutta stage 0..2
   int ta, ts;           // tile: lines x faces

@@ -452,8 +452,11 @@ __device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[
 // Ghost-cell map along the swept axis; s lies within one halo width of
 // [0, n) (n is at least the halo width), so the periodic wrap is one add or
 // subtract -- no integer division, whose 64-bit form runs on the FP64 unit.
+// A sub-domain's split axis (kBcHalo) keeps its ghost layers in the arrays,
+// next to the interior: positions outside [0, n) are read where they are.
 __device__ __forceinline__ long long bc_map(long long s, long long n, int bc) {
   if (bc == 0) return s < 0 ? s + n : (s >= n ? s - n : s);
+  if (bc == kBcHalo) return s;
   return s < 0 ? 0 : (s >= n ? n - 1 : s);
 }
 
@@ -488,6 +491,7 @@ __device__ __forceinline__ TileGeo tile_geo(const SweepArgs& A, long long tile) 
     g.base = b * n0; g.stride_a = 1; g.stride_d = n0 * n1;
     g.fbase = b * n0; g.fstride_a = 1; g.fstride_d = n0 * n1;
   }
+  g.base += A.org;  // sub-domains: the interior starts after the low ghost layers
   const long long left = g.nd - g.s0;
   g.nts = (int)(left < A.ts ? left : A.ts);
   return g;
