@@ -103,8 +103,11 @@ typedef struct {
  * gamma 1.4, adv_speed 1, delta 1e-5, tie_rel 1e-3, one cell per axis. */
 void enoao_config_default(enoao_config *cfg);
 
-/* Creates a context for one problem and allocates its device memory (three
- * state buffers and one right-hand-side buffer) on the current device.
+/* Creates a context for one problem -- the conservation law u_t + f(u)_x = 0
+ * on a uniform grid of n cells per axis (Sec. 2; dimension by dimension in 2D
+ * and 3D) -- and allocates its device memory (three state buffers: U^n and
+ * the two intermediate Runge-Kutta stages, and one right-hand-side buffer) on
+ * the current device.
  * cuda_stream: a cudaStream_t (may be 0).  Errors: ENOAO_EINVAL for an
  * invalid configuration (ndim not 1..3, order not 5 or 7, fewer cells along
  * a swept axis than the stencil needs (11), non-positive dx, gamma <= 1,
@@ -191,12 +194,16 @@ void enoao_destroy(enoao_ctx *ctx);
  * create, or of the last failed enoao_step_noalloc, on this host thread). */
 const char *enoao_last_error(const enoao_ctx *ctx);
 
-/* Sets the state U^n (conserved variables, layout above) and resets time and
- * step count.  Computes alpha of the new state.  ENOAO_ENONPHYS if the state
- * has rho <= 0, p <= 0 or NaN (Euler). */
+/* Sets the state U^n (conserved variables, layout above; for the Euler
+ * equations of Sec. 4 rho, momenta and total energy) and resets time and
+ * step count.  Computes alpha of the new state (Sec. 2: the maximum of
+ * |f'(u)| over the mesh), with the arithmetic the steps take it in.
+ * ENOAO_ENONPHYS if the state has rho <= 0, p <= 0 or NaN (Euler), with
+ * the first such cell in the message. */
 enoao_status enoao_init_state(enoao_ctx *ctx, const double *U, int on_device);
 
-/* Copies the current state U^n out (same layout). */
+/* Copies the current state U^n out (same layout): the numerical solution
+ * u_j of Sec. 2 at the time reached (enoao_get_stats). */
 enoao_status enoao_get_state(enoao_ctx *ctx, double *U, int on_device);
 
 /* Copies a Runge-Kutta stage state out (same layout): k = 0 is U^n (as
@@ -235,9 +242,10 @@ enoao_status enoao_rk_stage(enoao_ctx *ctx, int stage, double dt);
 enoao_status enoao_advance(enoao_ctx *ctx, double t_end, double cfl, double dt_fixed,
                            int64_t max_steps, double *t_out, int64_t *steps_out);
 
-/* Advances exactly nsteps steps with dt = cfl / sum_d(alpha_d / dx_d) (no
- * end time).  For batched contexts every problem takes nsteps steps with its
- * own alpha and dt in one persistent launch. */
+/* Advances exactly nsteps third-order TVD Runge-Kutta steps (Sec. 2) with
+ * dt = cfl / sum_d(alpha_d / dx_d), alpha from U^n of each step (no end
+ * time).  For batched contexts every problem takes nsteps steps with its own
+ * alpha and dt in one persistent launch. */
 enoao_status enoao_advance_steps(enoao_ctx *ctx, int64_t nsteps, double cfl);
 
 /* Same as enoao_advance_steps but only enqueues the work on the stream and
