@@ -292,6 +292,16 @@ enoao_status enoao_set_redecide(enoao_ctx *ctx, int mode);
 /* 1 when the context's steps use the grid-wide pass, else 0. */
 int enoao_uses_grid_redecide(const enoao_ctx *ctx);
 
+/* Whether FP32-bulk sweeps stage each tile's raw state (every component of
+ * the tile's cells and halo) into shared memory with one TMA bulk tensor copy
+ * per tile, issued a tile ahead (on = 1), or load it cell by cell (0, the
+ * default: measured faster on GB300, the box's shared memory costing more
+ * resident blocks than the copy saves).  Shapes TMA cannot address (row
+ * strides not a multiple of 16 bytes, boxes beyond 256 cells, sub-domains,
+ * the per-field and grid re-decision variants) load directly either way.
+ * The results are the same bits. */
+enoao_status enoao_set_tma(enoao_ctx *ctx, int on);
+
 /* Fault-injection knob for tests (the paper has no counterpart): bounds the
  * passes in which a warp re-decides its flagged FP32-bulk choices inside the
  * sweep (the default, -1, is 64 nv passes, which every warp needs at most

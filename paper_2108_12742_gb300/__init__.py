@@ -107,6 +107,7 @@ def load():
         "enoao_set_redecide": (ctypes.c_int, [P, ctypes.c_int]),
         "enoao_uses_grid_redecide": (ctypes.c_int, [P]),
         "enoao_set_redecide_pass_limit": (ctypes.c_int, [P, ctypes.c_int]),
+        "enoao_set_tma": (ctypes.c_int, [P, ctypes.c_int]),
         "enoao_get_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
         "enoao_autotune": (ctypes.c_int, [P]),
@@ -321,6 +322,10 @@ class Solver:
         """Where FP32-bulk near-ties are re-decided in FP64: REDECIDE_AUTO,
         REDECIDE_IN_SWEEP or REDECIDE_GRID (the grid-wide pass after each sweep)."""
         self._check(self._lib.enoao_set_redecide(self._h, mode))
+
+    def set_tma(self, on):
+        """FP32 bulk: stage raw tiles by TMA (True, default) or load them directly."""
+        self._check(self._lib.enoao_set_tma(self._h, 1 if on else 0))
 
     def set_redecide_pass_limit(self, passes):
         """Test knob: bound on the in-sweep FP64 re-decision passes (-1: default)."""

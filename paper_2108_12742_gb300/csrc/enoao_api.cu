@@ -1,7 +1,9 @@
 // Host runtime of the ENO-AO library: the C interface of include/enoao.h,
 // device buffers, the step kernels that keep alpha and dt on the device, CUDA
 // graph capture of whole steps, and the tile autotuner.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -356,6 +358,77 @@ enoao_status ensure_list(enoao_ctx* c) {
   return ENOAO_OK;
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// dependency on the driver library); NULL where it is not available.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// TMA staging of a sweep's raw tiles (the FP32-bulk sweep that re-decides its
+// near-ties itself): the stencil source u_in as a tensor of FP64 values --
+// (x, lines, components) for x sweeps, (x, y, z, components) otherwise -- and
+// the box of one tile, every component at once.  Returns false (direct loads)
+// where TMA cannot address the tiles: strides not a multiple of 16 bytes, box
+// edges beyond 256 cells, sub-domains, the per-field and listing variants.
+bool encode_tile_map(enoao_ctx* c, int d, bool list, const double* u_in, SweepArgs& a,
+                     CUtensorMap* map) {
+  if (!c->tma || !fp32(c) || list || consts(c).field || c->sub) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int G = halo(c->cfg.order), nv = c->nv;
+  const unsigned long long n0 = c->cfg.n[0], n1 = c->cfg.n[1], n2 = c->cfg.n[2];
+  const unsigned long long cs = (unsigned long long)c->carr * 8ull;
+  cuuint64_t dims[4], strides[3];
+  cuuint32_t box[4], es[4] = {1, 1, 1, 1};
+  int rank;
+  if (d == 0) {
+    int bx = a.ts + 2 * G + 1;  // one cell of slack: the box starts on an even x
+    bx += bx & 1;               // whole 16-byte rows
+    if (bx > 256) return false;
+    rank = 3;
+    dims[0] = n0, dims[1] = n1 * n2, dims[2] = nv;
+    strides[0] = n0 * 8ull, strides[1] = cs;
+    box[0] = bx, box[1] = a.ta, box[2] = nv;
+    a.tma_box = bx;
+  } else {
+    const int sb = a.ts + 2 * G;
+    if (sb > 256 || (a.ta & 1)) return false;
+    rank = 4;
+    dims[0] = n0, dims[1] = n1, dims[2] = n2, dims[3] = nv;
+    strides[0] = n0 * 8ull, strides[1] = n0 * n1 * 8ull, strides[2] = cs;
+    box[0] = a.ta, box[1] = d == 1 ? sb : 1, box[2] = d == 1 ? 1 : sb, box[3] = nv;
+    a.tma_box = sb;
+  }
+  for (int k = 0; k < rank - 1; ++k)
+    if (strides[k] % 16 != 0) return false;
+  if (reinterpret_cast<uintptr_t>(u_in) % 16 != 0) return false;
+  unsigned long long bytes = 8;
+  for (int k = 0; k < rank; ++k) bytes *= box[k];
+  a.tma_bytes = (unsigned)bytes;
+  a.tma_raw_bytes = (int)((bytes + 127) / 128 * 128);
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank, const_cast<double*>(u_in), dims,
+                         strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    a.tma_box = 0, a.tma_bytes = 0, a.tma_raw_bytes = 0;
+    return false;
+  }
+  return true;
+}
+
 // list: a stepping sweep (stage 0..2) of a context that uses the re-decision
 // list; the pass is launched right after the sweep (after recording
 // after_sweep, when given).
@@ -412,17 +485,22 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.delta = c->cfg.delta;
   a.tie_rel = c->cfg.tie_rel;
   a.redo_passes = c->redo_passes >= 0 ? c->redo_passes : 64 * c->nv;
-  const size_t smem = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts, a.se);
+  CUtensorMap tmap;
+  const size_t smem0 = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts, a.se);
+  bool tma = encode_tile_map(c, d, list, u_in, a, &tmap);
+  if (tma && smem0 + (size_t)a.tma_raw_bytes > 200 * 1024) tma = false;  // no room for the box
+  const size_t smem = smem0 + (tma ? (size_t)a.tma_raw_bytes : 0);
   const int block = c->block[d];
   int per_sm = 1;
   cudaError_t e;
   const int nv = c->nv, order = c->cfg.order;
   a.field = consts(c).field;
   if (fp32(c)) {
-    e = a.field ? sweep_configure_fp32_field(nv, order, smem) : sweep_configure_fp32(nv, order, smem);
+    e = a.field ? sweep_configure_fp32_field(nv, order, smem)
+                : sweep_configure_fp32(nv, order, smem, tma);
     if (e == cudaSuccess)
       e = a.field ? sweep_occupancy_fp32_field(nv, order, block, smem, &per_sm)
-                  : sweep_occupancy_fp32(nv, order, block, smem, &per_sm);
+                  : sweep_occupancy_fp32(nv, order, block, smem, &per_sm, tma);
   } else {
     e = a.field ? sweep_configure_fp64_field(nv, order, smem) : sweep_configure_fp64(nv, order, smem);
     if (e == cudaSuccess)
@@ -437,7 +515,8 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
     e = fp32(c) ? sweep_launch_fp32_field(nv, order, a, (int)grid, block, smem, c->s)
                 : sweep_launch_fp64_field(nv, order, a, (int)grid, block, smem, c->s);
   else
-    e = fp32(c) ? sweep_launch_fp32(nv, order, a, (int)grid, block, smem, c->s)
+    e = fp32(c) ? sweep_launch_fp32(nv, order, a, (int)grid, block, smem, c->s,
+                                    tma ? &tmap : nullptr)
                 : sweep_launch_fp64(nv, order, a, (int)grid, block, smem, c->s);
   if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
   if (after_sweep) CU(c, cudaEventRecord(after_sweep, c->s));
@@ -1087,6 +1166,16 @@ enoao_status enoao_set_redecide(enoao_ctx* c, int mode) {
 }
 
 int enoao_uses_grid_redecide(const enoao_ctx* c) { return c && use_list(c) ? 1 : 0; }
+
+enoao_status enoao_set_tma(enoao_ctx* c, int on) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  c->tma = on ? 1 : 0;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return ENOAO_OK;
+}
 
 enoao_status enoao_set_redecide_pass_limit(enoao_ctx* c, int passes) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");

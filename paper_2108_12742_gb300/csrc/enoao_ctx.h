@@ -46,6 +46,7 @@ struct enoao_ctx {
   unsigned* redo_mark = nullptr;       // per face
   long long redo_cap = 0;
   int redo_passes = -1;                // in-sweep re-decision pass bound (-1: 64 nv)
+  int tma = 0;                         // FP32 bulk: stage raw tiles by TMA where eligible
   // Arrays: carr cells per conserved component, the interior from cell org on.
   // A sub-domain (enoao_create_subdomain) owns layers [sub_off, sub_off + n[last])
   // of a grid split along its last axis and keeps halo() ghost layers on each

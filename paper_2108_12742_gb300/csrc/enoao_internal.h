@@ -89,6 +89,9 @@ struct SweepArgs {
   int ta, ts;           // tile: lines x faces
   int se;               // shared-memory row pitch in cells (sweep_row_pitch)
   int field;            // 1: per-field splitting constants (st->alpha_f), Euler only
+  int tma_box;          // TMA: box extent along the swept axis (cells, with alignment slack)
+  unsigned tma_bytes;   // TMA: bytes of one box
+  int tma_raw_bytes;    // TMA: shared memory reserved for the box (a multiple of 128)
   int redo_passes;      // FP32 bulk: bound on the in-sweep re-decision passes of a warp
                         // round; reaching it sets kErrTimeout (64 nv by default)
   long long tiles_s;    // tiles along dir
@@ -106,16 +109,20 @@ struct SweepArgs {
 // Host-side entry points of the instantiation units (sweep_fp64.cu,
 // sweep_fp32.cu); return cudaError_t values.
 }  // namespace enoao
+#include <cuda.h>
 #include <cuda_runtime.h>
 namespace enoao {
+// tmap: the stencil source as a tensor map for TMA staging of raw tiles (FP32
+// bulk sweeps that re-decide in the sweep), or NULL for direct loads.
 cudaError_t sweep_launch_fp64(int nv, int order, const SweepArgs& a, int grid, int block,
                               size_t smem, cudaStream_t s);
 cudaError_t sweep_launch_fp32(int nv, int order, const SweepArgs& a, int grid, int block,
-                              size_t smem, cudaStream_t s);
+                              size_t smem, cudaStream_t s, const CUtensorMap* tmap = nullptr);
 cudaError_t sweep_configure_fp64(int nv, int order, size_t smem);
-cudaError_t sweep_configure_fp32(int nv, int order, size_t smem);
+cudaError_t sweep_configure_fp32(int nv, int order, size_t smem, bool tma = false);
 cudaError_t sweep_occupancy_fp64(int nv, int order, int block, size_t smem, int* per_sm);
-cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm);
+cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm,
+                                 bool tma = false);
 cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cudaStream_t s);
 // per-field splitting constants (a.field; Euler systems, nv 3..5)
 cudaError_t sweep_launch_fp64_field(int nv, int order, const SweepArgs& a, int grid, int block,

@@ -34,6 +34,7 @@
 
 #include "enoao_internal.h"
 #include "state_speed.cuh"
+#include "tma.cuh"
 
 namespace enoao {
 
@@ -463,6 +464,7 @@ __device__ __forceinline__ long long bc_map(long long s, long long n, int bc) {
 // Geometry of one tile: cell(a, s) = base + (a0 + a) * stride_a + s * stride_d.
 struct TileGeo {
   long long s0, a0, base, stride_a, stride_d, na, nd;
+  long long b;                             // index along the remaining axis (dir != 0)
   long long fbase, fstride_a, fstride_d;  // same for the face array (nd + 1 faces)
   int nts;                                 // valid cells of the tile along dir
 };
@@ -478,6 +480,7 @@ __device__ __forceinline__ TileGeo tile_geo(const SweepArgs& A, long long tile) 
   const long long n0 = A.n[0], n1 = A.n[1], n2 = A.n[2];
   g.s0 = ts_i * A.ts;
   g.a0 = ta_i * A.ta;
+  g.b = b;
   if (A.dir == 0) {
     g.nd = n0; g.na = n1 * n2;
     g.base = 0; g.stride_a = n0; g.stride_d = 1;
@@ -821,18 +824,33 @@ __device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long c
 template <bool FIELD>
 constexpr int kAmax = FIELD ? 9 : 3;
 
+// The raw state of a tile staged in shared memory by TMA: conserved
+// component c of line a at extended cell e is p[c rc + a ra + (e + xoff) re]
+// (the layout of the copied box; xoff is the alignment slack of x boxes).
+struct RawTile {
+  const double* p = nullptr;
+  int rc = 0, ra = 0, re = 0, xoff = 0;
+};
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
 // constant of the swept axis and the step size; amax accumulates |u_d| + c of
 // combined states (last stage), nfall counts FP64 re-decisions.  FIELD: each
 // characteristic field splits with its own constant (st->alpha_f): phase 1
 // keeps dF/2 and dq/2, the split follows the projection, and the face's
 // centre part 1/2 R diag(alpha) L dq moves into its correction C.
+// TMA: phase 1 reads the tile's raw state from rt instead of global memory,
+// and hook() runs once every thread is past phase 1 (the raw buffer is then
+// free for the next tile's copy).
 template <int NV, int ORDER, typename R, bool COHERENT = false, bool DEFER = false,
-          bool FIELD = false>
+          bool FIELD = false, bool TMA = false, typename Hook = NoHook>
 __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
                                            unsigned char* smem_raw, double alpha_d, double dt,
                                            double (&amax)[kAmax<FIELD>],
-                                           unsigned long long& nfall) {
+                                           unsigned long long& nfall, const RawTile& rt = RawTile{},
+                                           Hook hook = Hook{}) {
   static_assert(!FIELD || NV >= 3, "per-field constants are for the Euler equations");
   using GE = Geo<ORDER>;
   constexpr int G = GE::G;
@@ -1009,9 +1027,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
     for_items(lgTA, cnt, sfast, [&](const int a, const int e) {
       if (g.a0 + a >= g.na) return;
       const long long la = g.base + (g.a0 + a) * g.stride_a;
-      const long long sa = bc_map(g.s0 - G + e, g.nd, A.bc);
       double qa64[NV];
-      load_state<NV, COHERENT>(A.u_in, A.cstride, la + sa * g.stride_d, dir, qa64);
+      // the tile's raw state: staged by TMA, or straight from global memory
+      auto cell_state = [&](int ee, double (&q)[NV]) {
+        if constexpr (TMA) {
+          const double* p = rt.p + a * rt.ra + (ee + rt.xoff) * rt.re;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) q[c] = p[perm_comp<NV>(c, dir) * rt.rc];
+        } else {
+          load_state<NV, COHERENT>(A.u_in, A.cstride,
+                                   la + bc_map(g.s0 - G + ee, g.nd, A.bc) * g.stride_d, dir, q);
+        }
+      };
+      cell_state(e, qa64);
       R qa[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) qa[c] = to_bulk<R>(qa64[c]);
@@ -1024,9 +1052,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         }
       }
       if (e + 1 < cnt) {
-        const long long sb = bc_map(g.s0 - G + e + 1, g.nd, A.bc);
         double qb64[NV];
-        load_state<NV, COHERENT>(A.u_in, A.cstride, la + sb * g.stride_d, dir, qb64);
+        cell_state(e + 1, qb64);
         R fp[NV], fm[NV];
         if constexpr (FIELD)
           split_parts<NV, R>(qa64, qb64, qa, gm1, adv, fp, fm);  // dF/2, dq/2
@@ -1038,6 +1065,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
     });
   }
   __syncthreads();
+  hook();
 
   // ---------------- phase 2: per face choice and back-projection
   {
@@ -1415,21 +1443,37 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #endif
 // Per-field splitting keeps two projections per window cell live and takes
 // four blocks (128 registers).
-template <int ORDER, typename R, bool FIELD = false>
+// With a TMA-staged raw tile a block needs more shared memory, and four of
+// them fill an SM: they get the registers (128, no spills; at 96 the
+// thread-0 copy issue spills).
+template <int ORDER, typename R, bool FIELD = false, bool TMA = false>
 constexpr int sweep_min_blocks() {
   return sizeof(R) == 8 ? 1
                         : (FIELD ? 4
-                                 : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5
-                                               : ENOAO_FP32_MIN_BLOCKS_AO7));
+                                 : (TMA ? 4
+                                        : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5
+                                                      : ENOAO_FP32_MIN_BLOCKS_AO7)));
 }
 
-template <int NV, int ORDER, typename R, bool DEFER = false, bool FIELD = false>
-__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD>())
-    sweep_kernel(const SweepArgs A) {
+// Bound on the polls of a TMA completion barrier (a copy of a few tens of KB
+// lands in microseconds; this is about a second): beyond it the kernel sets
+// the error word and returns instead of spinning on.
+constexpr long long kTmaPollLimit = 1ll << 24;
+
+// TMA: the tile's raw state (every component, the tile's lines, its cells and
+// halo along the swept axis) is one box of the tensor map tmap, copied into
+// the first A.tma_raw_bytes of dynamic shared memory by thread 0; the copy of
+// the next tile is issued as soon as phase 1 of the current one is done, so
+// it lands while phases 2 and 3 run.  Ghost cells outside the grid (the box
+// reads zeros there) are then filled from the boundary map with plain loads.
+template <int NV, int ORDER, typename R, bool DEFER = false, bool FIELD = false, bool TMA = false>
+__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD, TMA>())
+    sweep_kernel(const SweepArgs A, const __grid_constant__ CUtensorMap tmap) {
   constexpr bool FP32 = sizeof(R) == 4;
+  constexpr int G = Geo<ORDER>::G;
   StepState* st = A.st;
   if (st->skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int mode = A.mode;
   const double alpha_d = st->alpha[A.dir];
   const double dt = st->dt;
@@ -1442,13 +1486,98 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD>())
   // discontinuities), so blocks pull the next tile instead of striding.  The
   // last block to leave resets the queue for the next launch on the stream.
   __shared__ long long s_tile;
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&st->tile_next, 1ull);
+  if constexpr (!TMA) {
+    for (;;) {
+      if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&st->tile_next, 1ull);
+      __syncthreads();
+      const long long tile = s_tile;
+      if (tile >= A.ntiles) break;
+      sweep_tile<NV, ORDER, R, false, DEFER, FIELD>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax,
+                                                     nfall);
+    }
+  } else {
+    __shared__ __align__(8) unsigned long long s_bar;
+    double* raw = reinterpret_cast<double*>(smem_raw);
+    unsigned char* smem = smem_raw + A.tma_raw_bytes;
+    const int bx = A.tma_box;  // box extent along the swept axis
+    RawTile rt;
+    rt.p = raw;
+    if (A.dir == 0) {  // box (x, lines, components)
+      rt.re = 1, rt.ra = bx, rt.rc = bx * A.ta;
+    } else {           // box (x = lines, [y,] swept axis, [z,] components)
+      rt.re = A.ta, rt.ra = 1, rt.rc = A.ta * bx;
+    }
+    // thread 0: tile t's box on its way (x boxes start on the even x at or
+    // below the tile's first extended cell, 16-byte aligned)
+    auto issue = [&](long long t) {
+      const TileGeo gg = tile_geo(A, t);
+      const long long s_lo = gg.s0 - G;  // first extended cell along the swept axis
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&s_bar, A.tma_bytes);
+      if (A.dir == 0)
+        tma_load_3d(raw, &tmap, (int)(s_lo - (s_lo & 1)), (int)gg.a0, 0, &s_bar);
+      else if (A.dir == 1)
+        tma_load_4d(raw, &tmap, (int)gg.a0, (int)s_lo, (int)gg.b, 0, &s_bar);
+      else
+        tma_load_4d(raw, &tmap, (int)gg.a0, (int)gg.b, (int)s_lo, 0, &s_bar);
+    };
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar, 1);
+      const long long t = (long long)atomicAdd(&st->tile_next, 1ull);
+      s_tile = t;
+      if (t < A.ntiles) issue(t);
+    }
     __syncthreads();
-    const long long tile = s_tile;
-    if (tile >= A.ntiles) break;
-    sweep_tile<NV, ORDER, R, false, DEFER, FIELD>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax,
-                                                   nfall);
+    unsigned phase = 0;
+    for (;;) {
+      const long long tile = s_tile;
+      if (tile >= A.ntiles) break;
+      // the tile's box: a bounded wait, the same decision for the whole block
+      bool late = true;
+      for (long long it = 0; it < kTmaPollLimit; ++it)
+        if (mbar_try_wait(&s_bar, phase)) {
+          late = false;
+          break;
+        }
+      if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) atomicOr(&st->err, kErrTimeout);
+        // the copy may still be in flight into this block's shared memory:
+        // wait for it once more, again bounded, before leaving
+        for (long long it = 0; it < kTmaPollLimit && !mbar_try_wait(&s_bar, phase); ++it) {
+        }
+        break;
+      }
+      phase ^= 1;
+      const TileGeo g = tile_geo(A, tile);
+      rt.xoff = A.dir == 0 ? (int)((g.s0 - G) & 1) : 0;
+      // ghost cells beyond the grid along the swept axis (edge tiles only)
+      if (g.s0 - G < 0 || g.s0 + g.nts + G > g.nd) {
+        const int lgTA = __ffs(A.ta) - 1;
+        for_items(lgTA, 2 * G, A.dir == 0, [&](const int a, const int k) {
+          if (g.a0 + a >= g.na) return;
+          const int e = k < G ? k : g.nts + k;
+          const long long sg = g.s0 - G + e;
+          if (sg >= 0 && sg < g.nd) return;
+          double q[NV];
+          load_state<NV, false>(A.u_in, A.cstride,
+                                g.base + (g.a0 + a) * g.stride_a + bc_map(sg, g.nd, A.bc) * g.stride_d,
+                                A.dir, q);
+          double* p = raw + a * rt.ra + (e + rt.xoff) * rt.re;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) p[perm_comp<NV>(c, A.dir) * rt.rc] = q[c];
+        });
+        __syncthreads();
+      }
+      auto hook = [&]() {
+        if (threadIdx.x == 0) {
+          const long long t = (long long)atomicAdd(&st->tile_next, 1ull);
+          s_tile = t;
+          if (t < A.ntiles) issue(t);
+        }
+      };
+      sweep_tile<NV, ORDER, R, false, DEFER, FIELD, true>(A, g, smem, alpha_d, dt, amax, nfall, rt,
+                                                          hook);
+    }
   }
   if (threadIdx.x == 0) {
     __threadfence();

@@ -3,6 +3,8 @@
 // ENOAO_FIELD_R; included by sweep_fp32_field.cu and sweep_fp64_field.cu.
 #include "sweep.cuh"
 
+#include <cstring>
+
 namespace enoao {
 namespace {
 
@@ -10,7 +12,9 @@ using FR = ENOAO_FIELD_R;
 
 template <int NV, int ORDER>
 cudaError_t launch_field(const SweepArgs& a, int grid, int block, size_t smem, cudaStream_t s) {
-  sweep_kernel<NV, ORDER, FR, false, true><<<grid, block, smem, s>>>(a);
+  CUtensorMap none;  // direct loads: the map is not read
+  memset(&none, 0, sizeof none);
+  sweep_kernel<NV, ORDER, FR, false, true><<<grid, block, smem, s>>>(a, none);
   return cudaGetLastError();
 }
 

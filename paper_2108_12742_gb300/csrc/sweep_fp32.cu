@@ -2,30 +2,43 @@
 // FP32 (state and Runge-Kutta combine in FP64).
 #include "sweep.cuh"
 
+#include <cstring>
+
 namespace enoao {
 
 // Two variants per system and order: the sweep that re-decides its near-ties
 // itself, and the one that lists them for the grid-wide pass (a.redo set).
+// Three variants per system and order: the sweep that re-decides its
+// near-ties itself (raw tiles loaded directly, or staged by TMA when tmap is
+// given), and the one that lists them for the grid-wide pass (a.redo set).
 template <int NV, int ORDER>
 static cudaError_t launch_one(const SweepArgs& a, int grid, int block, size_t smem,
-                              cudaStream_t s) {
+                              cudaStream_t s, const CUtensorMap* tmap) {
+  CUtensorMap none;
+  memset(&none, 0, sizeof none);
   if (a.redo)
-    sweep_kernel<NV, ORDER, float, true><<<grid, block, smem, s>>>(a);
+    sweep_kernel<NV, ORDER, float, true><<<grid, block, smem, s>>>(a, none);
+  else if (tmap)
+    sweep_kernel<NV, ORDER, float, false, false, true><<<grid, block, smem, s>>>(a, *tmap);
   else
-    sweep_kernel<NV, ORDER, float, false><<<grid, block, smem, s>>>(a);
+    sweep_kernel<NV, ORDER, float, false><<<grid, block, smem, s>>>(a, none);
   return cudaGetLastError();
 }
 
 template <int NV, int ORDER>
-static cudaError_t configure_one(size_t smem) {
+static cudaError_t configure_one(size_t smem, bool tma) {
+  if (tma) return raise_smem_limit(sweep_kernel<NV, ORDER, float, false, false, true>, smem);
   cudaError_t e = raise_smem_limit(sweep_kernel<NV, ORDER, float, false>, smem);
   if (e == cudaSuccess) e = raise_smem_limit(sweep_kernel<NV, ORDER, float, true>, smem);
   return e;
 }
 
-// The smaller of the two variants' resident blocks per SM.
+// Resident blocks per SM: the TMA variant, or the smaller of the other two.
 template <int NV, int ORDER>
-static cudaError_t occupancy_one(int block, size_t smem, int* per_sm) {
+static cudaError_t occupancy_one(int block, size_t smem, int* per_sm, bool tma) {
+  if (tma)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        per_sm, sweep_kernel<NV, ORDER, float, false, false, true>, block, smem);
   int p0 = 0, p1 = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &p0, sweep_kernel<NV, ORDER, float, false>, block, smem);
@@ -50,8 +63,8 @@ static cudaError_t occupancy_one(int block, size_t smem, int* per_sm) {
   }
 
 cudaError_t sweep_launch_fp32(int nv, int order, const SweepArgs& a, int grid, int block,
-                              size_t smem, cudaStream_t s) {
-  ENOAO_DISPATCH(launch_one, a, grid, block, smem, s)
+                              size_t smem, cudaStream_t s, const CUtensorMap* tmap) {
+  ENOAO_DISPATCH(launch_one, a, grid, block, smem, s, tmap)
 }
 
 template <int NV, int ORDER>
@@ -69,12 +82,12 @@ cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cu
   ENOAO_DISPATCH(redo_one, a, grid, s)
 }
 
-cudaError_t sweep_configure_fp32(int nv, int order, size_t smem) {
-  ENOAO_DISPATCH(configure_one, smem)
+cudaError_t sweep_configure_fp32(int nv, int order, size_t smem, bool tma) {
+  ENOAO_DISPATCH(configure_one, smem, tma)
 }
 
-cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm) {
-  ENOAO_DISPATCH(occupancy_one, block, smem, per_sm)
+cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm, bool tma) {
+  ENOAO_DISPATCH(occupancy_one, block, smem, per_sm, tma)
 }
 
 }  // namespace enoao

@@ -2,12 +2,16 @@
 // FP64 (every step of the path in double precision).
 #include "sweep.cuh"
 
+#include <cstring>
+
 namespace enoao {
 
 template <int NV, int ORDER>
 static cudaError_t launch_one(const SweepArgs& a, int grid, int block, size_t smem,
                               cudaStream_t s) {
-  sweep_kernel<NV, ORDER, double><<<grid, block, smem, s>>>(a);
+  CUtensorMap none;  // direct loads: the map is not read
+  memset(&none, 0, sizeof none);
+  sweep_kernel<NV, ORDER, double><<<grid, block, smem, s>>>(a, none);
   return cudaGetLastError();
 }
 

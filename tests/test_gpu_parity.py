@@ -495,3 +495,44 @@ def test_grid_redecide_on_riemann_slip_lines(order):
             assert s.stats().fp64_fallbacks > 100, s.stats().fp64_fallbacks
             first[mode] = G[1]
     assert relerr(first[eno.REDECIDE_GRID], first[eno.REDECIDE_IN_SWEEP]) <= TOL32_STEP
+
+
+# ------------------------------------------------ TMA staging of raw tiles
+TMA_CASES = {
+    # shapes TMA can address (even x extent and component stride), both edges
+    "euler1d-334-ao7": ((334,), (0.0,), (1.0,), eno.EULER, 7, eno.TRANSMISSIVE,
+                        lambda: inputs.euler1d_riemann(334, seed=5)),
+    "euler2d-70x45-ao5": ((70, 45), (0.0, 0.0), (1.0, 1.0), eno.EULER, 5, eno.TRANSMISSIVE,
+                          lambda: inputs.euler2d_quadrants(70, 45, seed=1)),
+    "euler2d-40x38-ao7-periodic": ((40, 38), (0.0, 0.0), (1.0, 1.0), eno.EULER, 7, eno.PERIODIC,
+                                   lambda: inputs.euler2d_random(40, 38, seed=2)),
+    "euler3d-20x18x16-ao7": ((20, 18, 16), (0.0,) * 3, (1.0,) * 3, eno.EULER, 7, eno.PERIODIC,
+                             lambda: inputs.euler3d_blast(20, seed=3)[:, :16, :18, :20].copy()),
+    "euler3d-20x18x16-ao5-transmissive": ((20, 18, 16), (0.0,) * 3, (1.0,) * 3, eno.EULER, 5,
+                                          eno.TRANSMISSIVE,
+                                          lambda: inputs.euler3d_blast(20, seed=4)[:, :16, :18, :20].copy()),
+    "adv2d-34x30-ao5": ((34, 30), (0.0, 0.0), (1.0, 1.0), eno.SCALAR_ADVECTION, 5, eno.PERIODIC,
+                        lambda: inputs.advection_random(34 * 30, seed=4).reshape(1, 1, 30, 34)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TMA_CASES))
+def test_tma_staged_tiles_give_the_same_bits(name):
+    # the FP32-bulk sweeps with each tile's raw state copied into shared
+    # memory by TMA (ghost cells beyond the grid patched from the boundary
+    # map) against direct loads: the same arithmetic on the same values,
+    # fluxes of every axis and whole steps
+    shape, lo, hi, system, order, bc, init = TMA_CASES[name]
+    U0 = np.ascontiguousarray(init())
+    out = []
+    for tma in (False, True):
+        with eno.Solver(shape, lo, hi, system=system, order=order, bc=bc,
+                        precision=eno.FP32_BULK) as s:
+            s.set_tma(tma)
+            s.init_state(U0)
+            res = [s.reconstruct_fluxes(d, want_idx=True) for d in range(len(shape))]
+            s.advance(1e9, cfl=0.5, max_steps=3)
+            out.append((res, s.get_state()))
+    for (F0, i0), (F1, i1) in zip(out[0][0], out[1][0]):
+        assert np.array_equal(F0, F1) and np.array_equal(i0, i1), name
+    assert np.array_equal(out[0][1], out[1][1]), name
