@@ -496,11 +496,22 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   const int nv = c->nv, order = c->cfg.order;
   a.field = consts(c).field;
   if (fp32(c)) {
+    // ENO-AO5 tiles that let seven blocks share an SM take the LEAN kernel
+    // (re-decisions out of line, 72 registers); measured faster there
+    if (!a.field && !list && !tma && order == 5 && smem * 7 <= 220 * 1024) {
+      int lean_per_sm = 0;
+      if (sweep_configure_fp32(nv, order, smem, 2) == cudaSuccess &&
+          sweep_occupancy_fp32(nv, order, block, smem, &lean_per_sm, 2) == cudaSuccess &&
+          lean_per_sm >= 7)
+        a.lean = 1;
+      cudaGetLastError();
+    }
+    const int variant = tma ? 1 : (a.lean ? 2 : 0);
     e = a.field ? sweep_configure_fp32_field(nv, order, smem)
-                : sweep_configure_fp32(nv, order, smem, tma);
+                : sweep_configure_fp32(nv, order, smem, variant);
     if (e == cudaSuccess)
       e = a.field ? sweep_occupancy_fp32_field(nv, order, block, smem, &per_sm)
-                  : sweep_occupancy_fp32(nv, order, block, smem, &per_sm, tma);
+                  : sweep_occupancy_fp32(nv, order, block, smem, &per_sm, variant);
   } else {
     e = a.field ? sweep_configure_fp64_field(nv, order, smem) : sweep_configure_fp64(nv, order, smem);
     if (e == cudaSuccess)

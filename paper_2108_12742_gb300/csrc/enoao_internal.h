@@ -89,6 +89,7 @@ struct SweepArgs {
   int ta, ts;           // tile: lines x faces
   int se;               // shared-memory row pitch in cells (sweep_row_pitch)
   int field;            // 1: per-field splitting constants (st->alpha_f), Euler only
+  int lean;             // FP32 bulk, ENO-AO5, in-sweep re-decision: the seven-block variant
   int tma_box;          // TMA: box extent along the swept axis (cells, with alignment slack)
   unsigned tma_bytes;   // TMA: bytes of one box
   int tma_raw_bytes;    // TMA: shared memory reserved for the box (a multiple of 128)
@@ -119,10 +120,11 @@ cudaError_t sweep_launch_fp64(int nv, int order, const SweepArgs& a, int grid, i
 cudaError_t sweep_launch_fp32(int nv, int order, const SweepArgs& a, int grid, int block,
                               size_t smem, cudaStream_t s, const CUtensorMap* tmap = nullptr);
 cudaError_t sweep_configure_fp64(int nv, int order, size_t smem);
-cudaError_t sweep_configure_fp32(int nv, int order, size_t smem, bool tma = false);
+// variant: 0 the regular in-sweep / listing kernels, 1 TMA staging, 2 LEAN
+cudaError_t sweep_configure_fp32(int nv, int order, size_t smem, int variant = 0);
 cudaError_t sweep_occupancy_fp64(int nv, int order, int block, size_t smem, int* per_sm);
 cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm,
-                                 bool tma = false);
+                                 int variant = 0);
 cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cudaStream_t s);
 // per-field splitting constants (a.field; Euler systems, nv 3..5)
 cudaError_t sweep_launch_fp64_field(int nv, int order, const SweepArgs& a, int grid, int block,

@@ -824,84 +824,33 @@ __device__ __forceinline__ void bulk_state_check(const SweepArgs& A, long long c
 template <bool FIELD>
 constexpr int kAmax = FIELD ? 9 : 3;
 
-// The raw state of a tile staged in shared memory by TMA: conserved
-// component c of line a at extended cell e is p[c rc + a ra + (e + xoff) re]
-// (the layout of the copied box; xoff is the alignment slack of x boxes).
-struct RawTile {
-  const double* p = nullptr;
-  int rc = 0, ra = 0, re = 0, xoff = 0;
-};
-struct NoHook {
-  __device__ __forceinline__ void operator()() const {}
-};
-
-// One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
-// constant of the swept axis and the step size; amax accumulates |u_d| + c of
-// combined states (last stage), nfall counts FP64 re-decisions.  FIELD: each
-// characteristic field splits with its own constant (st->alpha_f): phase 1
-// keeps dF/2 and dq/2, the split follows the projection, and the face's
-// centre part 1/2 R diag(alpha) L dq moves into its correction C.
-// TMA: phase 1 reads the tile's raw state from rt instead of global memory,
-// and hook() runs once every thread is past phase 1 (the raw buffer is then
-// free for the next tile's copy).
-template <int NV, int ORDER, typename R, bool COHERENT = false, bool DEFER = false,
-          bool FIELD = false, bool TMA = false, typename Hook = NoHook>
-__device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
-                                           unsigned char* smem_raw, double alpha_d, double dt,
-                                           double (&amax)[kAmax<FIELD>],
-                                           unsigned long long& nfall, const RawTile& rt = RawTile{},
-                                           Hook hook = Hook{}) {
-  static_assert(!FIELD || NV >= 3, "per-field constants are for the Euler equations");
+// The shared-memory planes of a tile (per extended cell: the split
+// differences df+ and df-, the face correction C, the Roe ingredients and,
+// in FP32 bulk, one word of near-tie flags) and the projected windows of its
+// faces, shared by the tile's phases and the out-of-line re-decision.
+template <int NV, int ORDER, typename R, bool FIELD>
+struct TileView {
   using GE = Geo<ORDER>;
-  constexpr int G = GE::G;
-  constexpr bool FP32 = sizeof(R) == 4;
-  constexpr int NP = NPrim<NV>::value;
-  StepState* st = A.st;
-  const int TA = A.ta, TS = A.ts;
-  const int SE = A.se;  // row pitch (>= TS + 2G), chosen on the host for conflict-free banks
-  const int cells = TA * SE;
-  R* dfp = reinterpret_cast<R*>(smem_raw);
-  R* dfm = dfp + NV * cells;
-  R* Cf = dfm + NV * cells;
-  R* prim = Cf + NV * cells;
-  // FP32 only: near-tie flags per face (one word per cell slot)
-  unsigned* fixmask = reinterpret_cast<unsigned*>(prim + NP * cells);
-
-  const int dir = A.dir;
-  const bool sfast = dir == 0;
-  const R alpha = (R)alpha_d;
-  const R halpha = R(0.5) * alpha;
-  // splitting constant of field v: alpha, or per field max |u_d - c|, |u_d|, |u_d + c|
-  R alo = alpha, amid = alpha, ahi = alpha;
-  if constexpr (FIELD) {
-    alo = (R)st->alpha_f[A.dir][0];
-    amid = (R)st->alpha_f[A.dir][1];
-    ahi = (R)st->alpha_f[A.dir][2];
-  }
-  auto afield = [&](int v) { return v == 0 ? alo : (v == NV - 1 ? ahi : amid); };
-  // the same in FP64, for the re-decisions of near-ties
-  auto alpha64 = [&](int v) {
-    if constexpr (FIELD) return field_alpha<NV>(st, A.dir, v);
-    return alpha_d;
-  };
-  const R gm1 = (R)(A.gamma - 1.0);
-  const R adv = (R)A.adv_speed;
-  const R delta = (R)A.delta;
-  const R tie_rel = (R)A.tie_rel;
-  const int mode = A.mode;
-  const double inv_dx = A.inv_dx;
-  const R inv_dx_r = (R)inv_dx;
-  // Shared-memory rows of SE cells per line for every axis: unit stride
-  // along the swept axis (window offsets are immediates); SE is odd, so the
-  // y/z sweeps, whose lanes run across lines, hit distinct banks.
-  auto sidx = [&](int a, int e) { return a * SE + e; };
   using CV = CellVec<NV, R>;
-  const int lgTA = __ffs(TA) - 1;  // TA is a power of two (checked on the host)
-  (void)TS;
+  static constexpr bool FP32 = sizeof(R) == 4;
+  R* dfp;
+  R* dfm;
+  R* Cf;
+  R* prim;
+  unsigned* fixmask;
+  int cells, SE;
+  __device__ __forceinline__ TileView(unsigned char* smem_raw, int ta, int se) : cells(ta * se), SE(se) {
+    dfp = reinterpret_cast<R*>(smem_raw);
+    dfm = dfp + NV * cells;
+    Cf = dfm + NV * cells;
+    prim = Cf + NV * cells;
+    fixmask = reinterpret_cast<unsigned*>(prim + NPrim<NV>::value * cells);
+  }
+  __device__ __forceinline__ int sidx(int a, int e) const { return a * SE + e; }
   // Projected window of face j (extended cells) onto the field with left
   // eigenvector row L: sign 0 is the f^+ window centred on cell j, sign 1 the
   // mirrored f^- window centred on cell j+1 (d[i] = -(L df^-) at j+4-i).
-  auto window = [&](int a, int j, int sgn, const R (&L)[NV], R (&d)[8]) {
+  __device__ __forceinline__ void window(int a, int j, int sgn, const R (&L)[NV], R (&d)[8]) const {
     const R* src = sgn == 0 ? dfp : dfm;
 #pragma unroll
     for (int i = 0; i < 8; ++i) d[i] = R(0);
@@ -915,9 +864,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       for (int c = 0; c < NV; ++c) acc += L[c] * x[c];
       d[i] = sgn == 0 ? acc : -acc;
     }
-  };
+  }
   // the same window with the magnitudes sum_c |L_c| |df_c| of its terms
-  auto window_mag = [&](int a, int j, int sgn, const R (&L)[NV], R (&d)[8], R (&m)[8]) {
+  __device__ __forceinline__ void window_mag(int a, int j, int sgn, const R (&L)[NV], R (&d)[8],
+                                             R (&m)[8]) const {
     const R* src = sgn == 0 ? dfp : dfm;
 #pragma unroll
     for (int i = 0; i < 8; ++i) d[i] = m[i] = R(0);
@@ -935,10 +885,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       d[i] = sgn == 0 ? acc : -acc;
       m[i] = mag;
     }
-  };
+  }
   // The same for shear field v, whose left row is e_v - w e_0 (w its
   // tangential Roe velocity): one multiply-add per difference instead of NV.
-  auto window_shear = [&](int a, int j, int sgn, int v, R w, R (&d)[8], R (&m)[8]) {
+  __device__ __forceinline__ void window_shear(int a, int j, int sgn, int v, R w, R (&d)[8],
+                                               R (&m)[8]) const {
     if constexpr (NV >= 4) {
       const R* src = sgn == 0 ? dfp : dfm;
 #pragma unroll
@@ -954,12 +905,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         if constexpr (FP32) m[i] = rabs(xv) + rabs(w) * rabs(x[0]);
       }
     }
-  };
+  }
   // Per-field windows: dfp / dfm hold dF/2 and dq/2; field v splits after the
   // projection, d = L dF/2 +- alpha_v L dq/2 (sign 0: +, sign 1: mirrored -),
   // with magnitude sum |L||dF/2| + alpha_v sum |L||dq/2| for the near-tie bound.
-  auto window_field = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R av,
-                          R (&d)[8], R (&m)[8]) {
+  __device__ __forceinline__ void window_field(int a, int j, int sgn, int v, const R (&L)[NV], R w,
+                                               R av, R (&d)[8], R (&m)[8]) const {
     const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
     const R sa = sgn == 0 ? av : -av;
 #pragma unroll
@@ -997,11 +948,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       d[i] = sgn == 0 ? acc : -acc;
       m[i] = fma(av, mq, mF);
     }
-  };
+  }
   // Projected window of field v (the same arithmetic in phase 2 and in the
   // phase-2b check of a flagged choice, which must reproduce its pick).
-  auto field_window = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R av, R (&d)[8],
-                          R (&mag)[8]) {
+  __device__ __forceinline__ void field_window(int a, int j, int sgn, int v, const R (&L)[NV], R w,
+                                               R av, R (&d)[8], R (&mag)[8]) const {
     const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
     if constexpr (FIELD) {
       window_field(a, j, sgn, v, L, w, av, d, mag);
@@ -1017,172 +968,70 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 #pragma unroll
       for (int i = 0; i < 8; ++i) mag[i] = R(0);
     }
-  };
+  }
+};
+
+// The raw state of a tile staged in shared memory by TMA: conserved
+// component c of line a at extended cell e is p[c rc + a ra + (e + xoff) re]
+// (the layout of the copied box; xoff is the alignment slack of x boxes).
+struct RawTile {
+  const double* p = nullptr;
+  int rc = 0, ra = 0, re = 0, xoff = 0;
+};
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// One tile of a sweep (phases 1-3 above).  alpha_d and dt are the splitting
+// constant of the swept axis and the step size; amax accumulates |u_d| + c of
+// combined states (last stage), nfall counts FP64 re-decisions.  FIELD: each
+// characteristic field splits with its own constant (st->alpha_f): phase 1
+// keeps dF/2 and dq/2, the split follows the projection, and the face's
+// centre part 1/2 R diag(alpha) L dq moves into its correction C.
+// Phase 2b of a tile (FP32 bulk, near-ties re-decided in the sweep): the
+// flagged choices are re-decided from the FP64 state by lane groups of the
+// warp (redo_group), or lane by lane when a warp has many (redo_lane), then
+// each face applies the changes of its chosen values to its correction C in a
+// fixed field/sign order.  Out of line: only tiles with flagged choices call
+// it, and its FP64 code does not raise the register footprint of the common
+// path.  Ends with a block barrier.
+template <int NV, int ORDER, bool COHERENT, bool FIELD>
+__device__ __forceinline__ void redecide_tile(const SweepArgs& A, const TileGeo& g,
+                                              unsigned char* smem_raw, double alpha_d,
+                                              unsigned long long& nfall) {
+  using R = float;
+  using GE = Geo<ORDER>;
+  using CV = CellVec<NV, R>;
+  constexpr int G = GE::G;
+  StepState* st = A.st;
+  const int TA = A.ta, SE = A.se;
+  const TileView<NV, ORDER, R, FIELD> tv(smem_raw, TA, SE);
+  R* Cf = tv.Cf;
+  R* prim = tv.prim;
+  unsigned* fixmask = tv.fixmask;
+  const int cells = tv.cells;
+  auto sidx = [&](int a, int e) { return a * SE + e; };
+  const bool sfast = A.dir == 0;
+  const int lgTA = __ffs(TA) - 1;
   const int nts = g.nts;
-  const int sext = nts + 2 * G;  // extended cells in use
-
-  // ---------------- phase 1: split differences and Roe ingredients
-  {
-    const int cnt = sext;
-    for_items(lgTA, cnt, sfast, [&](const int a, const int e) {
-      if (g.a0 + a >= g.na) return;
-      const long long la = g.base + (g.a0 + a) * g.stride_a;
-      double qa64[NV];
-      // the tile's raw state: staged by TMA, or straight from global memory
-      auto cell_state = [&](int ee, double (&q)[NV]) {
-        if constexpr (TMA) {
-          const double* p = rt.p + a * rt.ra + (ee + rt.xoff) * rt.re;
-#pragma unroll
-          for (int c = 0; c < NV; ++c) q[c] = p[perm_comp<NV>(c, dir) * rt.rc];
-        } else {
-          load_state<NV, COHERENT>(A.u_in, A.cstride,
-                                   la + bc_map(g.s0 - G + ee, g.nd, A.bc) * g.stride_d, dir, q);
-        }
-      };
-      cell_state(e, qa64);
-      R qa[NV];
-#pragma unroll
-      for (int c = 0; c < NV; ++c) qa[c] = to_bulk<R>(qa64[c]);
-      const int si = sidx(a, e);
-      if constexpr (NP > 0) {
-        if (e >= G - 1 && e <= G + nts) {
-          R pr[NV];
-          roe_prims<NV, R>(qa, gm1, pr);
-          CV::store(prim, cells, si, pr);
-        }
-      }
-      if (e + 1 < cnt) {
-        double qb64[NV];
-        cell_state(e + 1, qb64);
-        R fp[NV], fm[NV];
-        if constexpr (FIELD)
-          split_parts<NV, R>(qa64, qb64, qa, gm1, adv, fp, fm);  // dF/2, dq/2
-        else
-          split_diff<NV, R>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
-        CV::store(dfp, cells, si, fp);
-        CV::store(dfm, cells, si, fm);
-      }
-    });
+  const int mode = A.mode;
+  const R gm1 = (R)(A.gamma - 1.0);
+  const R delta = (R)A.delta;
+  const R tie_rel = (R)A.tie_rel;
+  const R alpha = (R)alpha_d;
+  R alo = alpha, amid = alpha, ahi = alpha;
+  if constexpr (FIELD) {
+    alo = (R)st->alpha_f[A.dir][0];
+    amid = (R)st->alpha_f[A.dir][1];
+    ahi = (R)st->alpha_f[A.dir][2];
   }
-  __syncthreads();
-  hook();
-
-  // ---------------- phase 2: per face choice and back-projection
-  {
-    const int cnt = nts + 1;
-    for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
-      if (g.a0 + a >= g.na) return;
-      const int j = G - 1 + f;  // face j+1/2 in extended cells
-      Eigen<NV, R> E;
-      if constexpr (NV > 1) {
-        R pl[NV], prr[NV];
-        CV::load(prim, cells, sidx(a, j), pl);
-        CV::load(prim, cells, sidx(a, j + 1), prr);
-        roe_eigen<NV, R>(pl, prr, gm1, E);
-      }
-      const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
-      const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
-      R C[NV];
-#pragma unroll
-      for (int c = 0; c < NV; ++c) C[c] = R(0);
-      unsigned fix = 0;
-#pragma unroll 1
-      for (int v = 0; v < NV; ++v) {
-        // shear fields (2D/3D Euler) have a sparse left row e_v - w e_0
-        const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
-        R L[NV], w = R(0);
-        if constexpr (NV > 1) {
-          left_row<NV, R>(E, v, L);
-          if constexpr (NV >= 4) w = -L[0];
-        } else {
-          L[0] = R(1);
-        }
-        // f^+ then mirrored f^- window, one live at a time
-        R cv = R(0);
-        const R av = afield(v);
-        if constexpr (FIELD) {
-          // the face's centre part: - alpha_v L dq/2 of the face's own pair
-          R xq[NV];
-          CV::load(dfm, cells, sidx(a, j), xq);
-          R aq = R(0);
-          if constexpr (NV >= 4) {
-            if (shear) aq = shear_comp<NV>(xq, v) - w * xq[0];
-          }
-          if (!shear) {
-#pragma unroll
-            for (int c = 0; c < NV; ++c) aq += L[c] * xq[c];
-          }
-          cv = -av * aq;
-        }
-#pragma unroll
-        for (int sgn = 0; sgn < 2; ++sgn) {
-          R d[8], mag[8];
-          field_window(a, j, sgn, v, L, w, av, d, mag);
-          int pick;
-          bool marg = false;
-          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
-                                              pick, marg);
-          if constexpr (FP32) {
-            if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 (phase 2b or the pass)
-          }
-          if ((mode & kModeFlux) && A.idx_out && own) {
-            const long long nf = A.nfaces;
-            const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
-            A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
-          }
-          cv += corr;
-        }
-        if constexpr (NV >= 4) {
-          if (shear) {
-            // column v of R is e_v + w e_{NV-1}
-#pragma unroll
-            for (int c = 2; c < NV - 1; ++c) C[c] += c == v ? cv : R(0);
-            C[NV - 1] += w * cv;
-            continue;
-          }
-        }
-        if constexpr (NV > 1) {
-          R Rc[NV];
-          right_col<NV, R>(E, v, Rc);
-#pragma unroll
-          for (int c = 0; c < NV; ++c) C[c] += Rc[c] * cv;
-        } else {
-          C[0] += cv;
-        }
-      }
-      const int sj = sidx(a, j);
-      CV::store(Cf, cells, sj, C);
-      if constexpr (FP32) fixmask[sj] = fix;
-    });
-  }
-  __syncthreads();
-
-  // ---------------- phase 2b (FP32 bulk, re-decision list): list the faces
-  // with flagged choices that this tile owns; the grid-wide pass corrects both
-  // cells of each, whichever tiles they lie in, so results do not depend on
-  // tiles.  Nothing here changes Cf: phase 3 uses the FP32 choices.
-  if constexpr (FP32 && DEFER) {
-    for_items(lgTA, nts + 1, sfast, [&](const int a, const int f) {
-      if (g.a0 + a >= g.na) return;
-      const unsigned fix = fixmask[sidx(a, G - 1 + f)];
-      const long long gface = g.s0 + f;
-      if (!fix || !((gface <= g.nd) && (f < A.ts || gface == g.nd))) return;
-      const unsigned slot = atomicAdd(&st->redo_n, 1u);
-      if (slot < A.redo_cap) {
-        const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
-        A.redo[slot] = ((unsigned long long)fc << 16) | fix;
-      } else {
-        atomicOr(&st->err, kErrRedoFull);
-      }
-    });
-  }
-
-  // ---------------- phase 2b (FP32 bulk, no list): FP64 re-decision of near-ties
-  // Flagged choices are re-decided from the FP64 state by lane groups of the
-  // warp (redo_group), then each face applies the changes of its chosen values
-  // to its correction in a fixed field/sign order.  Kept out of phase 2 so the
-  // rare FP64 path does not raise the register footprint of the common one.
-  if constexpr (FP32 && !DEFER) {
+  auto afield = [&](int v) { return v == 0 ? alo : (v == NV - 1 ? ahi : amid); };
+  auto alpha64 = [&](int v) {
+    if constexpr (FIELD) return field_alpha<NV>(st, A.dir, v);
+    return alpha_d;
+  };
+  auto field_window = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R av, R (&d)[8],
+                          R (&mag)[8]) { tv.field_window(a, j, sgn, v, L, w, av, d, mag); };
     constexpr int W = 2 * G <= 8 ? 8 : 16;  // lanes per re-decision group
     const unsigned FULL = 0xffffffffu;
     const int cnt = nts + 1;
@@ -1326,7 +1175,254 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       for (int c = 0; c < NV; ++c) Cv[c] += dC[c];
       CV::store(Cf, cells, sj, Cv);
     }
-    __syncthreads();
+  __syncthreads();
+}
+
+// The same, not inlined (only one copy of the code, called by the tiles that
+// have flags): where the FP64 re-decision code would otherwise set the
+// register budget of the whole tile.
+template <int NV, int ORDER, bool COHERENT, bool FIELD>
+__device__ __noinline__ void redecide_tile_call(const SweepArgs& A, const TileGeo& g,
+                                                unsigned char* smem_raw, double alpha_d,
+                                                unsigned long long& nfall) {
+  redecide_tile<NV, ORDER, COHERENT, FIELD>(A, g, smem_raw, alpha_d, nfall);
+}
+
+// TMA: phase 1 reads the tile's raw state from rt instead of global memory,
+// and hook() runs once every thread is past phase 1 (the raw buffer is then
+// free for the next tile's copy).
+template <int NV, int ORDER, typename R, bool COHERENT = false, bool DEFER = false,
+          bool FIELD = false, bool TMA = false, typename Hook = NoHook, bool LEAN = false>
+__device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
+                                           unsigned char* smem_raw, double alpha_d, double dt,
+                                           double (&amax)[kAmax<FIELD>],
+                                           unsigned long long& nfall, const RawTile& rt = RawTile{},
+                                           Hook hook = Hook{}) {
+  static_assert(!FIELD || NV >= 3, "per-field constants are for the Euler equations");
+  using GE = Geo<ORDER>;
+  constexpr int G = GE::G;
+  constexpr bool FP32 = sizeof(R) == 4;
+  constexpr int NP = NPrim<NV>::value;
+  StepState* st = A.st;
+  const int TA = A.ta, TS = A.ts;
+  const int SE = A.se;  // row pitch (>= TS + 2G), chosen on the host for conflict-free banks
+  const int cells = TA * SE;
+  R* dfp = reinterpret_cast<R*>(smem_raw);
+  R* dfm = dfp + NV * cells;
+  R* Cf = dfm + NV * cells;
+  R* prim = Cf + NV * cells;
+  // FP32 only: near-tie flags per face (one word per cell slot)
+  unsigned* fixmask = reinterpret_cast<unsigned*>(prim + NP * cells);
+
+  const int dir = A.dir;
+  const bool sfast = dir == 0;
+  const R alpha = (R)alpha_d;
+  const R halpha = R(0.5) * alpha;
+  // splitting constant of field v: alpha, or per field max |u_d - c|, |u_d|, |u_d + c|
+  R alo = alpha, amid = alpha, ahi = alpha;
+  if constexpr (FIELD) {
+    alo = (R)st->alpha_f[A.dir][0];
+    amid = (R)st->alpha_f[A.dir][1];
+    ahi = (R)st->alpha_f[A.dir][2];
+  }
+  auto afield = [&](int v) { return v == 0 ? alo : (v == NV - 1 ? ahi : amid); };
+  // the same in FP64, for the re-decisions of near-ties
+  auto alpha64 = [&](int v) {
+    if constexpr (FIELD) return field_alpha<NV>(st, A.dir, v);
+    return alpha_d;
+  };
+  const R gm1 = (R)(A.gamma - 1.0);
+  const R adv = (R)A.adv_speed;
+  const R delta = (R)A.delta;
+  const R tie_rel = (R)A.tie_rel;
+  const int mode = A.mode;
+  const double inv_dx = A.inv_dx;
+  const R inv_dx_r = (R)inv_dx;
+  // Shared-memory rows of SE cells per line for every axis: unit stride
+  // along the swept axis (window offsets are immediates); SE is odd, so the
+  // y/z sweeps, whose lanes run across lines, hit distinct banks.
+  auto sidx = [&](int a, int e) { return a * SE + e; };
+  using CV = CellVec<NV, R>;
+  const int lgTA = __ffs(TA) - 1;  // TA is a power of two (checked on the host)
+  (void)TS;
+  const TileView<NV, ORDER, R, FIELD> tv(smem_raw, TA, SE);
+  // Projected window of field v (the same arithmetic in phase 2 and in the
+  // phase-2b check of a flagged choice, which must reproduce its pick).
+  auto field_window = [&](int a, int j, int sgn, int v, const R (&L)[NV], R w, R av, R (&d)[8],
+                          R (&mag)[8]) { tv.field_window(a, j, sgn, v, L, w, av, d, mag); };
+  const int nts = g.nts;
+  const int sext = nts + 2 * G;  // extended cells in use
+
+  // ---------------- phase 1: split differences and Roe ingredients
+  {
+    const int cnt = sext;
+    for_items(lgTA, cnt, sfast, [&](const int a, const int e) {
+      if (g.a0 + a >= g.na) return;
+      const long long la = g.base + (g.a0 + a) * g.stride_a;
+      double qa64[NV];
+      // the tile's raw state: staged by TMA, or straight from global memory
+      auto cell_state = [&](int ee, double (&q)[NV]) {
+        if constexpr (TMA) {
+          const double* p = rt.p + a * rt.ra + (ee + rt.xoff) * rt.re;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) q[c] = p[perm_comp<NV>(c, dir) * rt.rc];
+        } else {
+          load_state<NV, COHERENT>(A.u_in, A.cstride,
+                                   la + bc_map(g.s0 - G + ee, g.nd, A.bc) * g.stride_d, dir, q);
+        }
+      };
+      cell_state(e, qa64);
+      R qa[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) qa[c] = to_bulk<R>(qa64[c]);
+      const int si = sidx(a, e);
+      if constexpr (NP > 0) {
+        if (e >= G - 1 && e <= G + nts) {
+          R pr[NV];
+          roe_prims<NV, R>(qa, gm1, pr);
+          CV::store(prim, cells, si, pr);
+        }
+      }
+      if (e + 1 < cnt) {
+        double qb64[NV];
+        cell_state(e + 1, qb64);
+        R fp[NV], fm[NV];
+        if constexpr (FIELD)
+          split_parts<NV, R>(qa64, qb64, qa, gm1, adv, fp, fm);  // dF/2, dq/2
+        else
+          split_diff<NV, R>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
+        CV::store(dfp, cells, si, fp);
+        CV::store(dfm, cells, si, fm);
+      }
+    });
+  }
+  __syncthreads();
+  hook();
+
+  // ---------------- phase 2: per face choice and back-projection
+  bool any_fix = false;  // FP32 bulk: this thread flagged a near-tie
+  {
+    const int cnt = nts + 1;
+    for_items(lgTA, cnt, sfast, [&](const int a, const int f) {
+      if (g.a0 + a >= g.na) return;
+      const int j = G - 1 + f;  // face j+1/2 in extended cells
+      Eigen<NV, R> E;
+      if constexpr (NV > 1) {
+        R pl[NV], prr[NV];
+        CV::load(prim, cells, sidx(a, j), pl);
+        CV::load(prim, cells, sidx(a, j + 1), prr);
+        roe_eigen<NV, R>(pl, prr, gm1, E);
+      }
+      const long long gface = g.s0 + f;  // face index between cells gface-1 and gface
+      const bool own = (gface <= g.nd) && (f < A.ts || gface == g.nd);
+      R C[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) C[c] = R(0);
+      unsigned fix = 0;
+#pragma unroll 1
+      for (int v = 0; v < NV; ++v) {
+        // shear fields (2D/3D Euler) have a sparse left row e_v - w e_0
+        const bool shear = NV >= 4 && v >= 2 && v <= NV - 2;
+        R L[NV], w = R(0);
+        if constexpr (NV > 1) {
+          left_row<NV, R>(E, v, L);
+          if constexpr (NV >= 4) w = -L[0];
+        } else {
+          L[0] = R(1);
+        }
+        // f^+ then mirrored f^- window, one live at a time
+        R cv = R(0);
+        const R av = afield(v);
+        if constexpr (FIELD) {
+          // the face's centre part: - alpha_v L dq/2 of the face's own pair
+          R xq[NV];
+          CV::load(dfm, cells, sidx(a, j), xq);
+          R aq = R(0);
+          if constexpr (NV >= 4) {
+            if (shear) aq = shear_comp<NV>(xq, v) - w * xq[0];
+          }
+          if (!shear) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) aq += L[c] * xq[c];
+          }
+          cv = -av * aq;
+        }
+#pragma unroll
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          R d[8], mag[8];
+          field_window(a, j, sgn, v, L, w, av, d, mag);
+          int pick;
+          bool marg = false;
+          R corr = eno_select<ORDER, R, FP32>(d, delta, tie_rel, mag, R(NV + 8) * R(FLT_EPSILON),
+                                              pick, marg);
+          if constexpr (FP32) {
+            if (marg) fix |= 1u << (v * 2 + sgn);  // re-decided in FP64 (phase 2b or the pass)
+          }
+          if ((mode & kModeFlux) && A.idx_out && own) {
+            const long long nf = A.nfaces;
+            const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+            A.idx_out[(v * 2 + sgn) * nf + fc] = (int8_t)pick;
+          }
+          cv += corr;
+        }
+        if constexpr (NV >= 4) {
+          if (shear) {
+            // column v of R is e_v + w e_{NV-1}
+#pragma unroll
+            for (int c = 2; c < NV - 1; ++c) C[c] += c == v ? cv : R(0);
+            C[NV - 1] += w * cv;
+            continue;
+          }
+        }
+        if constexpr (NV > 1) {
+          R Rc[NV];
+          right_col<NV, R>(E, v, Rc);
+#pragma unroll
+          for (int c = 0; c < NV; ++c) C[c] += Rc[c] * cv;
+        } else {
+          C[0] += cv;
+        }
+      }
+      const int sj = sidx(a, j);
+      CV::store(Cf, cells, sj, C);
+      if constexpr (FP32) {
+        fixmask[sj] = fix;
+        any_fix |= fix != 0u;
+      }
+    });
+  }
+  if constexpr (!(FP32 && !DEFER)) __syncthreads();  // else the barrier of phase 2b's test
+
+  // ---------------- phase 2b (FP32 bulk, re-decision list): list the faces
+  // with flagged choices that this tile owns; the grid-wide pass corrects both
+  // cells of each, whichever tiles they lie in, so results do not depend on
+  // tiles.  Nothing here changes Cf: phase 3 uses the FP32 choices.
+  if constexpr (FP32 && DEFER) {
+    for_items(lgTA, nts + 1, sfast, [&](const int a, const int f) {
+      if (g.a0 + a >= g.na) return;
+      const unsigned fix = fixmask[sidx(a, G - 1 + f)];
+      const long long gface = g.s0 + f;
+      if (!fix || !((gface <= g.nd) && (f < A.ts || gface == g.nd))) return;
+      const unsigned slot = atomicAdd(&st->redo_n, 1u);
+      if (slot < A.redo_cap) {
+        const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
+        A.redo[slot] = ((unsigned long long)fc << 16) | fix;
+      } else {
+        atomicOr(&st->err, kErrRedoFull);
+      }
+    });
+  }
+
+  // ---------------- phase 2b (FP32 bulk, no list): FP64 re-decision of near-ties
+  // Only tiles with flagged choices run it.  LEAN kernels call it out of line,
+  // so that its FP64 code does not set the register budget of every tile.
+  if constexpr (FP32 && !DEFER) {
+    if (__syncthreads_or(any_fix)) {
+      if constexpr (LEAN)
+        redecide_tile_call<NV, ORDER, COHERENT, FIELD>(A, g, smem_raw, alpha_d, nfall);
+      else
+        redecide_tile<NV, ORDER, COHERENT, FIELD>(A, g, smem_raw, alpha_d, nfall);
+    }
   }
 
   // ---------------- phase 3: flux difference and Runge-Kutta combine
@@ -1446,13 +1542,16 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 // With a TMA-staged raw tile a block needs more shared memory, and four of
 // them fill an SM: they get the registers (128, no spills; at 96 the
 // thread-0 copy issue spills).
-template <int ORDER, typename R, bool FIELD = false, bool TMA = false>
+// LEAN (ENO-AO5 in-sweep re-decision, re-decisions out of line): seven
+// blocks, 72 registers, for tiles whose shared memory lets seven fit.
+template <int ORDER, typename R, bool FIELD = false, bool TMA = false, bool LEAN = false>
 constexpr int sweep_min_blocks() {
   return sizeof(R) == 8 ? 1
                         : (FIELD ? 4
                                  : (TMA ? 4
-                                        : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5
-                                                      : ENOAO_FP32_MIN_BLOCKS_AO7)));
+                                        : (LEAN ? 7
+                                                : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5
+                                                              : ENOAO_FP32_MIN_BLOCKS_AO7))));
 }
 
 // Bound on the polls of a TMA completion barrier (a copy of a few tens of KB
@@ -1466,9 +1565,10 @@ constexpr long long kTmaPollLimit = 1ll << 24;
 // the next tile is issued as soon as phase 1 of the current one is done, so
 // it lands while phases 2 and 3 run.  Ghost cells outside the grid (the box
 // reads zeros there) are then filled from the boundary map with plain loads.
-template <int NV, int ORDER, typename R, bool DEFER = false, bool FIELD = false, bool TMA = false>
-__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD, TMA>())
-    sweep_kernel(const SweepArgs A, const __grid_constant__ CUtensorMap tmap) {
+template <int NV, int ORDER, typename R, bool DEFER = false, bool FIELD = false, bool TMA = false,
+          bool LEAN = false>
+__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD, TMA, LEAN>())
+    sweep_kernel(const __grid_constant__ SweepArgs A, const __grid_constant__ CUtensorMap tmap) {
   constexpr bool FP32 = sizeof(R) == 4;
   constexpr int G = Geo<ORDER>::G;
   StepState* st = A.st;
@@ -1492,8 +1592,8 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD, TMA>())
       __syncthreads();
       const long long tile = s_tile;
       if (tile >= A.ntiles) break;
-      sweep_tile<NV, ORDER, R, false, DEFER, FIELD>(A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax,
-                                                     nfall);
+      sweep_tile<NV, ORDER, R, false, DEFER, FIELD, false, NoHook, LEAN>(
+          A, tile_geo(A, tile), smem_raw, alpha_d, dt, amax, nfall);
     }
   } else {
     __shared__ __align__(8) unsigned long long s_bar;

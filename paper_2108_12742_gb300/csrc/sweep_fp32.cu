@@ -11,6 +11,12 @@ namespace enoao {
 // Three variants per system and order: the sweep that re-decides its
 // near-ties itself (raw tiles loaded directly, or staged by TMA when tmap is
 // given), and the one that lists them for the grid-wide pass (a.redo set).
+// The LEAN kernel (ENO-AO5 only): re-decisions out of line, seven blocks.
+template <int NV, int ORDER>
+static auto lean_kernel() {
+  return sweep_kernel<NV, ORDER, float, false, false, false, ORDER == 5>;
+}
+
 template <int NV, int ORDER>
 static cudaError_t launch_one(const SweepArgs& a, int grid, int block, size_t smem,
                               cudaStream_t s, const CUtensorMap* tmap) {
@@ -20,25 +26,32 @@ static cudaError_t launch_one(const SweepArgs& a, int grid, int block, size_t sm
     sweep_kernel<NV, ORDER, float, true><<<grid, block, smem, s>>>(a, none);
   else if (tmap)
     sweep_kernel<NV, ORDER, float, false, false, true><<<grid, block, smem, s>>>(a, *tmap);
+  else if (a.lean && ORDER == 5)
+    lean_kernel<NV, ORDER>()<<<grid, block, smem, s>>>(a, none);
   else
     sweep_kernel<NV, ORDER, float, false><<<grid, block, smem, s>>>(a, none);
   return cudaGetLastError();
 }
 
 template <int NV, int ORDER>
-static cudaError_t configure_one(size_t smem, bool tma) {
-  if (tma) return raise_smem_limit(sweep_kernel<NV, ORDER, float, false, false, true>, smem);
+static cudaError_t configure_one(size_t smem, int variant) {
+  if (variant == 1) return raise_smem_limit(sweep_kernel<NV, ORDER, float, false, false, true>, smem);
+  if (variant == 2) return raise_smem_limit(lean_kernel<NV, ORDER>(), smem);
   cudaError_t e = raise_smem_limit(sweep_kernel<NV, ORDER, float, false>, smem);
   if (e == cudaSuccess) e = raise_smem_limit(sweep_kernel<NV, ORDER, float, true>, smem);
   return e;
 }
 
-// Resident blocks per SM: the TMA variant, or the smaller of the other two.
+// Resident blocks per SM: the TMA or LEAN variant, or the smaller of the
+// other two.
 template <int NV, int ORDER>
-static cudaError_t occupancy_one(int block, size_t smem, int* per_sm, bool tma) {
-  if (tma)
+static cudaError_t occupancy_one(int block, size_t smem, int* per_sm, int variant) {
+  if (variant == 1)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         per_sm, sweep_kernel<NV, ORDER, float, false, false, true>, block, smem);
+  if (variant == 2)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, lean_kernel<NV, ORDER>(), block,
+                                                         smem);
   int p0 = 0, p1 = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &p0, sweep_kernel<NV, ORDER, float, false>, block, smem);
@@ -82,12 +95,13 @@ cudaError_t redo_launch_fp32(int nv, int order, const SweepArgs& a, int grid, cu
   ENOAO_DISPATCH(redo_one, a, grid, s)
 }
 
-cudaError_t sweep_configure_fp32(int nv, int order, size_t smem, bool tma) {
-  ENOAO_DISPATCH(configure_one, smem, tma)
+cudaError_t sweep_configure_fp32(int nv, int order, size_t smem, int variant) {
+  ENOAO_DISPATCH(configure_one, smem, variant)
 }
 
-cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm, bool tma) {
-  ENOAO_DISPATCH(occupancy_one, block, smem, per_sm, tma)
+cudaError_t sweep_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm,
+                                 int variant) {
+  ENOAO_DISPATCH(occupancy_one, block, smem, per_sm, variant)
 }
 
 }  // namespace enoao
