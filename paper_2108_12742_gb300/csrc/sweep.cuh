@@ -383,12 +383,26 @@ __device__ __forceinline__ void roe_eigen(const T (&pl)[NV], const T (&prr)[NV],
   E.b2 = T(0.5) * q2 * E.b1;
 }
 
+// The constant c ? 1 : 0 (and c ? 1 : -1) by an integer select: a
+// floating-point select of constants can become a conversion instruction,
+// which issues to the FP64 unit.
+template <typename T>
+__device__ __forceinline__ T one_if(bool c) {
+  if constexpr (sizeof(T) == 4) return __int_as_float(c ? 0x3f800000 : 0);
+  return c ? T(1) : T(0);
+}
+template <typename T>
+__device__ __forceinline__ T sign_if(bool c) {
+  if constexpr (sizeof(T) == 4) return __int_as_float(c ? 0x3f800000 : (int)0xbf800000u);
+  return c ? T(1) : T(-1);
+}
+
 // Row v of L = R^{-1}; fields ordered (u-c, entropy, shear..., u+c).
 template <int NV, typename T>
 __device__ __forceinline__ void left_row(const Eigen<NV, T>& E, int v, T (&L)[NV]) {
   constexpr int NT = NV - 3;
   if (v == 0 || v == NV - 1) {
-    const T s = v == 0 ? T(1) : T(-1);
+    const T s = sign_if<T>(v == 0);
     L[0] = T(0.5) * (E.b2 + s * E.u * E.ic);
     L[1] = T(0.5) * (-E.b1 * E.u - s * E.ic);
 #pragma unroll
@@ -407,7 +421,7 @@ __device__ __forceinline__ void left_row(const Eigen<NV, T>& E, int v, T (&L)[NV
 #pragma unroll
     for (int t = 1; t < NT; ++t) w = v - 2 == t ? E.vt[t] : w;
 #pragma unroll
-    for (int i = 1; i < NV; ++i) L[i] = i == v ? T(1) : T(0);
+    for (int i = 1; i < NV; ++i) L[i] = one_if<T>(i == v);
     L[0] = -w;
   }
 }
@@ -428,7 +442,7 @@ template <int NV, typename T>
 __device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[NV]) {
   constexpr int NT = NV - 3;
   if (v == 0 || v == NV - 1) {
-    const T s = v == 0 ? T(-1) : T(1);
+    const T s = sign_if<T>(v != 0);
     Rc[0] = T(1);
     Rc[1] = E.u + s * E.c;
 #pragma unroll
@@ -445,7 +459,7 @@ __device__ __forceinline__ void right_col(const Eigen<NV, T>& E, int v, T (&Rc)[
 #pragma unroll
     for (int t = 1; t < NT; ++t) w = v - 2 == t ? E.vt[t] : w;
 #pragma unroll
-    for (int i = 0; i < NV - 1; ++i) Rc[i] = i == v ? T(1) : T(0);
+    for (int i = 0; i < NV - 1; ++i) Rc[i] = one_if<T>(i == v);
     Rc[NV - 1] = w;
   }
 }
@@ -1238,6 +1252,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
   const R inv_dx_r = (R)inv_dx;
+  // FP32 bulk combine: the stage's weight of dt L(u) (1, 1/4, 2/3) times dt
+  const float wdt32 = f32_rn((A.stage == 0 ? 1.0 : (A.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
   // Shared-memory rows of SE cells per line for every axis: unit stride
   // along the swept axis (window offsets are immediates); SE is odd, so the
   // y/z sweeps, whose lanes run across lines, hit distinct banks.
@@ -1489,15 +1505,30 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         // to FP64 for the Runge-Kutta combine
         R Lsum = r[c];
         if (mode & kModeRhsAdd) Lsum = reinterpret_cast<const R*>(A.rhs)[k] + r[c];
-        const double Lk = to_f64(Lsum);
         const double ui = A.u_in[k];
         double un;
-        if (A.stage == 0) {
-          un = ui + dt * Lk;
-        } else if (A.stage == 1) {
-          un = 0.75 * A.u0[k] + 0.25 * (ui + dt * Lk);
+        if constexpr (FP32) {
+          // The stage's increment w dt L(u) in FP32 (L is an FP32-bulk
+          // quantity; the product rounds once more at FP32), the Shu-Osher
+          // sums in FP64: u1 = u + dt L, u2 = 3/4 u0 + (1/4 u1 + 1/4 dt L),
+          // u3 = 1/3 u0 + (2/3 u2 + 2/3 dt L) as FP64 multiply-adds -- one or
+          // two operations on the FP64 unit instead of three.
+          const double inc = f64_of(wdt32 * Lsum);
+          if (A.stage == 0)
+            un = ui + inc;
+          else if (A.stage == 1)
+            un = fma(0.75, A.u0[k], fma(0.25, ui, inc));
+          else
+            un = fma(1.0 / 3.0, A.u0[k], fma(2.0 / 3.0, ui, inc));
         } else {
-          un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
+          const double Lk = to_f64(Lsum);
+          if (A.stage == 0) {
+            un = ui + dt * Lk;
+          } else if (A.stage == 1) {
+            un = 0.75 * A.u0[k] + 0.25 * (ui + dt * Lk);
+          } else {
+            un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
+          }
         }
         A.u_out[k] = un;
         up[c] = un;
