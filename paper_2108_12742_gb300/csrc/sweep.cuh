@@ -143,43 +143,20 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
 #pragma unroll
     for (int i = 0; i < 2; ++i) s7[i] = s6[i + 1] - s6[i];
   }
-  R IS[9];
-  // min(a/2, b/2) = min(a, b)/2 exactly (scaling by a power of two)
-  IS[0] = R(0.5) * rmin(rabs(d[3]) + rabs(d[2]), rabs(d[4]) + rabs(d[5]));
-  IS[1] = rmin(rabs(s2[3]), rabs(s2[4]));
-  IS[2] = rmin(rabs(s3[2]), rabs(s3[3]));
-  IS[3] = rmin(rabs(s4[1]), rabs(s4[2]));
-  IS[4] = rmin(rabs(s4[2]), rabs(s4[3]));
-  IS[5] = rmin(rabs(s5[1]), rabs(s5[2]));
-  if constexpr (ORDER == 7) {
-    IS[6] = rmin(rabs(s6[0]), rabs(s6[1]));
-    IS[7] = rmin(rabs(s6[1]), rabs(s6[2]));
-    IS[8] = rmin(rabs(s7[0]), rabs(s7[1]));
-  }
-  // Principle 1: the highest-priority candidate with IS <= delta.
-  int pick = -1;
+  // Principle 1 first for the top candidate (highest priority): at or below
+  // delta it is the pick whatever the other indicators are -- the smooth
+  // case, most windows -- and only its own rounding bound is needed.
   const auto kdelta = okey(delta);
-#pragma unroll
-  for (int c = 0; c < NC; ++c)
-    if (okey(IS[c]) <= kdelta) pick = c;
-  const bool thr = pick >= 0;
-  // Principle 2: otherwise the smallest IS, equal values to the higher priority.
-  R best = IS[0];
-  if (!thr) {
-    pick = 0;
-#pragma unroll
-    for (int c = 1; c < NC; ++c)
-      if (okey(IS[c]) <= okey(best)) {
-        best = IS[c];
-        pick = c;
-      }
-  }
-  if constexpr (CHECK) {
-    const R rel = tie_rel * delta;
-    bool m = false;
-    if (thr && pick == NC - 1) {
-      // top candidate below the threshold (smooth data): only it decides, and
-      // only its bound is formed (the Pascal sums below, written out)
+  R IS_top;
+  if constexpr (ORDER == 7)
+    IS_top = rmin(rabs(s7[0]), rabs(s7[1]));
+  else
+    IS_top = rmin(rabs(s5[1]), rabs(s5[2]));
+  int pick;
+  if (okey(IS_top) <= kdelta) {
+    pick = NC - 1;
+    if constexpr (CHECK) {
+      // its bound: the Pascal sums of e over its two differences, written out
       R qa, qb;
       if constexpr (ORDER == 7) {
         qa = e[0] + e[6] + R(6) * (e[1] + e[5]) + R(15) * (e[2] + e[4]) + R(20) * e[3];
@@ -188,8 +165,42 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
         qa = e[1] + e[5] + R(4) * (e[2] + e[4]) + R(6) * e[3];
         qb = e[2] + e[6] + R(4) * (e[3] + e[5]) + R(6) * e[4];
       }
-      m = rabs(IS[NC - 1] - delta) <= rel + feps * fmaxf(qa, qb);
-    } else {
+      marginal = rabs(IS_top - delta) <= tie_rel * delta + feps * fmaxf(qa, qb);
+    }
+  } else {
+    R IS[9];
+    // min(a/2, b/2) = min(a, b)/2 exactly (scaling by a power of two)
+    IS[0] = R(0.5) * rmin(rabs(d[3]) + rabs(d[2]), rabs(d[4]) + rabs(d[5]));
+    IS[1] = rmin(rabs(s2[3]), rabs(s2[4]));
+    IS[2] = rmin(rabs(s3[2]), rabs(s3[3]));
+    IS[3] = rmin(rabs(s4[1]), rabs(s4[2]));
+    IS[4] = rmin(rabs(s4[2]), rabs(s4[3]));
+    if constexpr (ORDER == 7) {
+      IS[5] = rmin(rabs(s5[1]), rabs(s5[2]));
+      IS[6] = rmin(rabs(s6[0]), rabs(s6[1]));
+      IS[7] = rmin(rabs(s6[1]), rabs(s6[2]));
+    }
+    IS[NC - 1] = IS_top;
+    // Principle 1 over the others (the top is above delta here).
+    pick = -1;
+#pragma unroll
+    for (int c = 0; c < NC - 1; ++c)
+      if (okey(IS[c]) <= kdelta) pick = c;
+    const bool thr = pick >= 0;
+    // Principle 2: otherwise the smallest IS, equal values to the higher priority.
+    R best = IS[0];
+    if (!thr) {
+      pick = 0;
+#pragma unroll
+      for (int c = 1; c < NC; ++c)
+        if (okey(IS[c]) <= okey(best)) {
+          best = IS[c];
+          pick = c;
+        }
+    }
+    if constexpr (CHECK) {
+      const R rel = tie_rel * delta;
+      bool m = false;
       // per-candidate bounds: Pascal sums of e over each indicator's differences
       R q2[8], q3[8], q4[8], q5[8], q6[8], q7[8];
 #pragma unroll
@@ -247,8 +258,8 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
 #pragma unroll
         for (int c = 0; c < NC; ++c) m |= (c != pick) && (gap[c] <= relA + tol[c]);
       }
+      marginal = m;
     }
-    marginal = m;
   }
   pick_out = pick;
   R corr = R(0);
