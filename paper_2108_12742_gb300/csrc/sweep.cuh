@@ -79,6 +79,21 @@ __device__ __forceinline__ double bcoef<double>(int c, int i) { return kB64[c][i
 template <>
 __device__ __forceinline__ float bcoef<float>(int c, int i) { return kB32[c][i]; }
 
+// Coefficient i of the top candidate (S_{j-2}^{j+2} of ENO-AO5, S_{j-3}^{j+3}
+// of ENO-AO7), the same values as its row of kB32 / kB64, as immediates.
+template <int ORDER, typename R>
+__device__ __forceinline__ R bcoef_top(int i) {
+  if constexpr (ORDER == 5) {
+    constexpr R b[8] = {R(0), R(0), R(-1) / R(30), R(11) / R(60), R(2) / R(5), R(-1) / R(20), R(0),
+                        R(0)};
+    return b[i];
+  } else {
+    constexpr R b[8] = {R(0),         R(1) / R(140), R(-11) / R(210), R(79) / R(420),
+                        R(3) / R(7), R(-17) / R(210), R(1) / R(105),  R(0)};
+    return b[i];
+  }
+}
+
 // Square root in the bulk precision (an unqualified sqrt on a float can
 // resolve to the double routine, which runs on the slow FP64 unit).
 __device__ __forceinline__ double bsqrt(double a) { return sqrt(a); }
@@ -128,33 +143,39 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
                                         R feps, int& pick_out, bool& marginal) {
   using GE = Geo<ORDER>;
   constexpr int LO = GE::LO, HI = GE::HI, NC = GE::NC;
-  R s2[8], s3[8], s4[8], s5[8], s6[8], s7[8];
-#pragma unroll
-  for (int i = LO; i < HI; ++i) s2[i] = d[i + 1] - d[i];
-#pragma unroll
-  for (int i = LO; i < HI - 1; ++i) s3[i] = s2[i + 1] - s2[i];
-#pragma unroll
-  for (int i = LO; i < HI - 2; ++i) s4[i] = s3[i + 1] - s3[i];
-#pragma unroll
-  for (int i = LO; i < HI - 3; ++i) s5[i] = s4[i + 1] - s4[i];
-  if constexpr (ORDER == 7) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) s6[i] = s5[i + 1] - s5[i];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) s7[i] = s6[i + 1] - s6[i];
-  }
   // Principle 1 first for the top candidate (highest priority): at or below
   // delta it is the pick whatever the other indicators are -- the smooth
-  // case, most windows -- and only its own rounding bound is needed.
+  // case, most windows -- and only its indicator, its rounding bound and its
+  // Table-1 value (compile-time coefficients) are needed.  Its two undivided
+  // differences of order 5 (7) are formed directly with their binomial
+  // weights; the difference table of the other candidates is built only when
+  // the top one is above delta.
   const auto kdelta = okey(delta);
   R IS_top;
-  if constexpr (ORDER == 7)
-    IS_top = rmin(rabs(s7[0]), rabs(s7[1]));
-  else
-    IS_top = rmin(rabs(s5[1]), rabs(s5[2]));
+  if constexpr (ORDER == 7) {
+    auto b6 = [&](int o) {  // sum_k (-1)^k C(6,k) d[o+k]
+      R t = d[o] + d[o + 6];
+      t = fma(R(-6), d[o + 1] + d[o + 5], t);
+      t = fma(R(15), d[o + 2] + d[o + 4], t);
+      return fma(R(-20), d[o + 3], t);
+    };
+    IS_top = rmin(rabs(b6(0)), rabs(b6(1)));
+  } else {
+    auto b4 = [&](int o) {  // sum_k (-1)^k C(4,k) d[o+k]
+      R t = d[o] + d[o + 4];
+      t = fma(R(-4), d[o + 1] + d[o + 3], t);
+      return fma(R(6), d[o + 2], t);
+    };
+    IS_top = rmin(rabs(b4(1)), rabs(b4(2)));
+  }
   int pick;
+  R corr = R(0);
   if (okey(IS_top) <= kdelta) {
     pick = NC - 1;
+    // its nonzero coefficients: d[2..5] (ENO-AO5), d[1..6] (ENO-AO7)
+#pragma unroll
+    for (int i = ORDER == 5 ? 2 : 1; i <= (ORDER == 5 ? 5 : 6); ++i)
+      corr += bcoef_top<ORDER, R>(i) * d[i];
     if constexpr (CHECK) {
       // its bound: the Pascal sums of e over its two differences, written out
       R qa, qb;
@@ -168,6 +189,19 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
       marginal = rabs(IS_top - delta) <= tie_rel * delta + feps * fmaxf(qa, qb);
     }
   } else {
+    R s2[8], s3[8], s4[8], s5[8], s6[8];
+#pragma unroll
+    for (int i = LO; i < HI; ++i) s2[i] = d[i + 1] - d[i];
+#pragma unroll
+    for (int i = LO; i < HI - 1; ++i) s3[i] = s2[i + 1] - s2[i];
+#pragma unroll
+    for (int i = LO; i < HI - 2; ++i) s4[i] = s3[i + 1] - s3[i];
+#pragma unroll
+    for (int i = LO; i < HI - 3; ++i) s5[i] = s4[i + 1] - s4[i];
+    if constexpr (ORDER == 7) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s6[i] = s5[i + 1] - s5[i];
+    }
     R IS[9];
     // min(a/2, b/2) = min(a, b)/2 exactly (scaling by a power of two)
     IS[0] = R(0.5) * rmin(rabs(d[3]) + rabs(d[2]), rabs(d[4]) + rabs(d[5]));
@@ -260,11 +294,10 @@ __device__ __forceinline__ R eno_select(const R (&d)[8], R delta, R tie_rel, con
       }
       marginal = m;
     }
+#pragma unroll
+    for (int i = LO; i <= HI; ++i) corr += bcoef<R>(pick, i) * d[i];
   }
   pick_out = pick;
-  R corr = R(0);
-#pragma unroll
-  for (int i = LO; i <= HI; ++i) corr += bcoef<R>(pick, i) * d[i];
   return corr;
 }
 
