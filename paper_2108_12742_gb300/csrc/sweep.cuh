@@ -118,13 +118,31 @@ __device__ __forceinline__ float okey(float a) { return a; }
 template <typename R>
 __device__ __forceinline__ R rmin(R a, R b) { return okey(a) < okey(b) ? a : b; }
 
+// Narrowing of a phase-1 input (an FP64 state component or the difference of
+// two) to FP32 in six integer operations: the exponent word is clamped at the
+// smallest normal FP32 exponent (so zero needs no branch), half an FP32 ulp
+// is added at mantissa bit 28 with the carry running into the exponent, and
+// the word is shifted into place with the exponent rebased from 1023 to 127.
+// Round to nearest for every magnitude in [2^-126, 2^128) (an exact tie
+// rounds away from zero); zero keeps its sign; a magnitude below 2^-126 gives
+// one below 2^-126.  Magnitudes of 2^128 and more are out of range: a state
+// that large fails the state check of its step, which narrows with f32_rn.
+// The hardware conversion issues to the FP64 unit and is slower here.
+__device__ __forceinline__ float f32_near(double x) {
+  const unsigned lo = __double2loint(x), hi = __double2hiint(x);
+  const unsigned hc = max(hi & 0x7FFFFFFFu, 896u << 20);
+  const unsigned long long w =
+      ((static_cast<unsigned long long>(hc - (896u << 20)) << 32) | lo) + 0x10000000ull;
+  return __uint_as_float(static_cast<unsigned>(w >> 29) | (hi & 0x80000000u));
+}
+
 // FP64 value in the bulk precision, and a bulk value widened to FP64.
 template <typename R>
 __device__ __forceinline__ R to_bulk(double x);
 template <>
 __device__ __forceinline__ double to_bulk<double>(double x) { return x; }
 template <>
-__device__ __forceinline__ float to_bulk<float>(double x) { return f32_rn(x); }
+__device__ __forceinline__ float to_bulk<float>(double x) { return f32_near(x); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f64_of(x); }
 
@@ -1868,8 +1886,8 @@ __device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo&
     float ql[NV], qr[NV], pl[NV], prr[NV];
 #pragma unroll
     for (int c = 0; c < NV; ++c) {
-      ql[c] = f32_rn(ql64[c]);
-      qr[c] = f32_rn(qr64[c]);
+      ql[c] = to_bulk<float>(ql64[c]);  // the sweep's phase-1 narrowing
+      qr[c] = to_bulk<float>(qr64[c]);
     }
     roe_prims<NV, float>(ql, gm1, pl);
     roe_prims<NV, float>(qr, gm1, prr);
@@ -1894,7 +1912,7 @@ __device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo&
     cell(c0 + 1, qb64);
     float qa[NV], fp[NV], fm[NV], x[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) qa[c] = f32_rn(qa64[c]);
+    for (int c = 0; c < NV; ++c) qa[c] = to_bulk<float>(qa64[c]);
     split_diff<NV, float>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
 #pragma unroll
     for (int c = 0; c < NV; ++c) x[c] = sgn == 0 ? fp[c] : fm[c];
