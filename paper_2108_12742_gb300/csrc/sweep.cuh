@@ -1539,26 +1539,36 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       if (g.a0 + a >= g.na) return;
       const int e = G + t;
       const long long cell = g.base + (g.a0 + a) * g.stride_a + (g.s0 + t) * g.stride_d;
-      R r[NV], p0[NV], m1[NV], c1[NV], c0[NV];
-      // per field: dF/2 of both of the cell's pairs (the centre part is in C)
-      CV::load(dfp, cells, sidx(a, e - 1), p0);
-      CV::load(FIELD ? dfp : dfm, cells, sidx(a, e), m1);
-      CV::load(Cf, cells, sidx(a, e), c1);
-      CV::load(Cf, cells, sidx(a, e - 1), c0);
+      R r[NV];
+      {
+        R p0[NV], m1[NV], c1[NV], c0[NV];
+        // per field: dF/2 of both of the cell's pairs (the centre part is in C)
+        CV::load(dfp, cells, sidx(a, e - 1), p0);
+        CV::load(FIELD ? dfp : dfm, cells, sidx(a, e), m1);
+        CV::load(Cf, cells, sidx(a, e), c1);
+        CV::load(Cf, cells, sidx(a, e - 1), c0);
 #pragma unroll
-      for (int c = 0; c < NV; ++c) {
-        const R s = p0[c] + m1[c] + (c1[c] - c0[c]);
-        r[c] = -s * inv_dx_r;
+        for (int c = 0; c < NV; ++c) {
+          const R s = p0[c] + m1[c] + (c1[c] - c0[c]);
+          r[c] = -s * inv_dx_r;
+        }
       }
+      // Every store of the cell comes after all its loads: the stores could
+      // alias the inputs as far as the compiler knows, so a load after a
+      // store would wait for it (one memory round trip per component).
       if (!(mode & kModeCombine)) {
         R* rb = reinterpret_cast<R*>(A.rhs);
+        R v[NV];
 #pragma unroll
         for (int c = 0; c < NV; ++c) {
           const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
-          rb[k] = (mode & kModeRhsAdd) ? rb[k] + r[c] : r[c];
+          v[c] = (mode & kModeRhsAdd) ? rb[k] + r[c] : r[c];
         }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) rb[perm_comp<NV>(c, dir) * A.cstride + cell] = v[c];
         return;
       }
+      auto u0v = [&](const double* p) { return COHERENT ? __ldcg(p) : __ldg(p); };
       double up[NV], unew[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
@@ -1567,7 +1577,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         // to FP64 for the Runge-Kutta combine
         R Lsum = r[c];
         if (mode & kModeRhsAdd) Lsum = reinterpret_cast<const R*>(A.rhs)[k] + r[c];
-        const double ui = A.u_in[k];
+        // (the batched kernel reads stage states it wrote itself: through L2)
+        const double ui = COHERENT ? __ldcg(A.u_in + k) : __ldg(A.u_in + k);
+        const double* u0p = A.u0 + k;
         double un;
         if constexpr (FP32) {
           // The stage's increment w dt L(u) in FP32 (L is an FP32-bulk
@@ -1579,22 +1591,23 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
           if (A.stage == 0)
             un = ui + inc;
           else if (A.stage == 1)
-            un = fma(0.75, A.u0[k], fma(0.25, ui, inc));
+            un = fma(0.75, u0v(u0p), fma(0.25, ui, inc));
           else
-            un = fma(1.0 / 3.0, A.u0[k], fma(2.0 / 3.0, ui, inc));
+            un = fma(1.0 / 3.0, u0v(u0p), fma(2.0 / 3.0, ui, inc));
         } else {
           const double Lk = to_f64(Lsum);
           if (A.stage == 0) {
             un = ui + dt * Lk;
           } else if (A.stage == 1) {
-            un = 0.75 * A.u0[k] + 0.25 * (ui + dt * Lk);
+            un = 0.75 * u0v(u0p) + 0.25 * (ui + dt * Lk);
           } else {
-            un = (1.0 / 3.0) * A.u0[k] + (2.0 / 3.0) * (ui + dt * Lk);
+            un = (1.0 / 3.0) * u0v(u0p) + (2.0 / 3.0) * (ui + dt * Lk);
           }
         }
-        A.u_out[k] = un;
         up[c] = un;
       }
+#pragma unroll
+      for (int c = 0; c < NV; ++c) A.u_out[perm_comp<NV>(c, dir) * A.cstride + cell] = up[c];
 #pragma unroll
       for (int k = 0; k < NV; ++k) unew[k] = comp_of<NV>(up, k, dir);  // conserved order
       if constexpr (FP32) {
