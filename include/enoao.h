@@ -330,8 +330,9 @@ enoao_status enoao_set_redecide_pass_limit(enoao_ctx *ctx, int passes);
  * U_in and U_out must be device memory of the current device (checked:
  * ENOAO_EINVAL otherwise); their size cannot be checked from a pointer, so
  * each must hold nv * n[0] doubles.
- * The two intermediate stage states and the step's device-side state live in
- * one fixed file-scope device array (12 MiB per GPU, held until the process
+ * The two intermediate stage states, the two FP32 stage increments of the
+ * FP32 bulk combine and the step's device-side state live in
+ * one fixed file-scope device array (18 MiB per GPU, held until the process
  * exits).  The first call on a device loads the library's device code there
  * (CUDA loads modules lazily by default), which brings the array into
  * existence, and looks up its device address (cudaGetSymbolAddress); make

@@ -23,6 +23,7 @@ namespace enoao {
 
 struct BatchArgs {
   double* U[3];            // U^n, U1, U2; [nv][total]
+  float* inc[2];           // FP32 bulk: stage increments I0, I1; [nv][total]
   long long total;         // cells of all problems (component stride)
   int nprob;
   int nsteps;
@@ -133,6 +134,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
         A.u_in = B.U[stage] + off;
         A.u0 = B.U[0] + off;
         A.u_out = B.U[stage == 2 ? 0 : stage + 1] + off;
+        A.inc_in = stage == 0 ? nullptr : B.inc[stage - 1] + off;
+        A.inc_out = stage == 2 ? nullptr : B.inc[stage] + off;
         A.stage = stage;
         A.mode = kModeCombine | (stage == 2 || per_stage ? kModeAlpha : 0);
         for (long long tile = 0; tile < A.ntiles; ++tile)
@@ -170,6 +173,7 @@ struct BatchState {
   double* dt = nullptr;
   int* queue = nullptr;
   double* U[3] = {nullptr, nullptr, nullptr};
+  float* inc[2] = {nullptr, nullptr};
   int ts = 256, block = 256;
   long long steps = 0;
   std::vector<long long> off_h;
@@ -254,6 +258,7 @@ BatchArgs make_args(enoao_ctx* c, int nsteps, double cfl) {
   BatchArgs a;
   memset(&a, 0, sizeof a);
   for (int k = 0; k < 3; ++k) a.U[k] = b->U[k];
+  for (int k = 0; k < 2; ++k) a.inc[k] = b->inc[k];
   a.total = b->total;
   a.nprob = b->nprob;
   a.nsteps = nsteps;
@@ -317,6 +322,7 @@ enoao_status read_err(enoao_ctx* c) {
 void batch_destroy(BatchState* b) {
   if (!b) return;
   for (int k = 0; k < 3; ++k) cudaFree(b->U[k]);
+  for (int k = 0; k < 2; ++k) cudaFree(b->inc[k]);
   cudaFree(b->order);
   cudaFree(b->off);
   cudaFree(b->n);
@@ -360,6 +366,8 @@ enoao_status batch_create(enoao_ctx* c, const enoao_config* proto, int nprob, co
   c->ncell = total;
   const size_t sb = (size_t)b->nv * total * sizeof(double);
   for (int k = 0; k < 3; ++k) BCU(c, cudaMalloc(&b->U[k], sb));
+  if (proto->precision == ENOAO_FP32_BULK)
+    for (int k = 0; k < 2; ++k) BCU(c, cudaMalloc(&b->inc[k], (size_t)b->nv * total * sizeof(float)));
   BCU(c, cudaMalloc(&b->order, nprob * sizeof(int)));
   BCU(c, cudaMalloc(&b->off, nprob * sizeof(long long)));
   BCU(c, cudaMalloc(&b->n, nprob * sizeof(int)));

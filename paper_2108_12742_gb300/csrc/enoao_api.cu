@@ -448,6 +448,9 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.u0 = c->U[0];
   a.u_out = u_out;
   a.rhs = c->rhs;
+  // FP32 bulk: stage 0 writes I0, stage 1 reads I0 and writes I1, stage 2 reads I1
+  a.inc_in = stage == 0 ? nullptr : c->inc[stage - 1];
+  a.inc_out = stage == 2 ? nullptr : c->inc[stage];
   a.fhat = fhat;
   a.idx_out = idx;
   a.st = c->st;
@@ -746,6 +749,8 @@ static enoao_status create_common(const enoao_config* cfg, void* stream, enoao_c
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->U[k], bytes);
     if (e == cudaSuccess && cfg->ndim > 1)
       e = cudaMalloc(&c->rhs, (size_t)c->nv * c->carr * (fp32(c) ? 4 : 8));
+    for (int k = 0; k < 2 && e == cudaSuccess && fp32(c); ++k)
+      e = cudaMalloc(&c->inc[k], (size_t)c->nv * c->carr * sizeof(float));
     if (e != cudaSuccess) {
       enoao_status r = fail(nullptr, e == cudaErrorMemoryAllocation ? ENOAO_ENOMEM : ENOAO_ECUDA,
                             "device allocation of %zu bytes per state failed: %s", bytes,
@@ -942,6 +947,7 @@ void enoao_destroy(enoao_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (int k = 0; k < 3; ++k) cudaFree(c->U[k]);
   cudaFree(c->rhs);
+  for (int k = 0; k < 2; ++k) cudaFree(c->inc[k]);
   cudaFree(c->redo);
   cudaFree(c->redo_dc);
   cudaFree(c->redo_mark);

@@ -30,6 +30,7 @@ struct enoao_ctx {
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, t0 = nullptr, t1 = nullptr;
   double* U[3] = {nullptr, nullptr, nullptr};  // U^n, U1, U2
   void* rhs = nullptr;
+  float* inc[2] = {nullptr, nullptr};  // FP32 bulk: stage increments I0, I1 ([nv][carr])
   enoao::StepState* st = nullptr;       // device
   enoao::StepState* st_host = nullptr;  // pinned mirror
   int ta[3] = {0, 0, 0}, ts[3] = {0, 0, 0}, block[3] = {128, 128, 128};

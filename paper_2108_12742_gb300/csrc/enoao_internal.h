@@ -64,6 +64,9 @@ struct SweepArgs {
   const double* u0;     // U^n for the Runge-Kutta combine
   double* u_out;        // combined state
   void* rhs;            // accumulated L(u) of earlier axes ([nv][N], bulk type)
+  const float* inc_in;  // FP32 bulk combine: the FP32 stage increment of the previous
+                        // stage ([nv][N], stages 1 and 2: I0 = dt L(U^n), I1 = I0 + dt L(U1))
+  float* inc_out;       // FP32 bulk combine: this stage's increment (stages 0 and 1)
   double* fhat;         // kModeFlux: interface fluxes [nv][faces]
   int8_t* idx_out;      // kModeFlux: choices [nv][2][faces] (nullable)
   unsigned long long* redo;  // FP32 bulk, stepping: faces listed for the grid-wide FP64

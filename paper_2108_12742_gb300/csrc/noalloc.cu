@@ -26,16 +26,17 @@ using namespace enoao;
 namespace {
 
 // Largest problem the fixed array can hold: 2^18 cells of at most three
-// conserved variables (1D Euler), two stage states -> 12 MiB of device memory
-// on every GPU on which the library is loaded, held until the process exits.
+// conserved variables (1D Euler), two FP64 stage states and two FP32 stage
+// increments -> 18 MiB of device memory on every GPU on which the library is
+// loaded, held until the process exits.
 constexpr long long kMaxCells = 1ll << 18;
 constexpr int kMaxNv = 3;
 constexpr long long kStateDoubles = kMaxNv * kMaxCells;
 constexpr long long kStepStateDoubles = (sizeof(StepState) + sizeof(double) - 1) / sizeof(double);
 static_assert(kStepStateDoubles <= 64, "StepState must fit its reserved slot");
 
-// [U1 | U2 | StepState slot]
-static __device__ __align__(256) double g_noalloc_scratch[2 * kStateDoubles + 64];
+// [U1 | U2 | I0 I1 (FP32) | StepState slot]
+static __device__ __align__(256) double g_noalloc_scratch[3 * kStateDoubles + 64];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -160,7 +161,9 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   const int nv = cfg->system == ENOAO_EULER ? 3 : 1;
   double* U1 = scratch;
   double* U2 = scratch + kStateDoubles;
-  StepState* st = reinterpret_cast<StepState*>(scratch + 2 * kStateDoubles);
+  float* I0 = reinterpret_cast<float*>(scratch + 2 * kStateDoubles);  // FP32 bulk increments
+  float* I1 = I0 + kStateDoubles;
+  StepState* st = reinterpret_cast<StepState*>(scratch + 3 * kStateDoubles);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -221,6 +224,8 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
     a.u_in = ins[stage];
     a.u0 = U_in;
     a.u_out = outs[stage];
+    a.inc_in = stage == 0 ? nullptr : (stage == 1 ? I0 : I1);
+    a.inc_out = stage == 0 ? I0 : (stage == 1 ? I1 : nullptr);
     a.stage = stage;
     a.mode = kModeCombine;
     e = f32 ? sweep_launch_fp32(nv, cfg->order, a, grid, block, smem, s)

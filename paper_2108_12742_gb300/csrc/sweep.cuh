@@ -1315,7 +1315,10 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   const double inv_dx = A.inv_dx;
   const R inv_dx_r = (R)inv_dx;
   // FP32 bulk combine: the stage's weight of dt L(u) (1, 1/4, 2/3) times dt
+  // FP32 bulk combine: dt and the stage's weight of dt L in FP32
+  const float dt32 = f32_rn(dt);
   const float wdt32 = f32_rn((A.stage == 0 ? 1.0 : (A.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
+  const float inc_w = A.stage == 1 ? -0.75f : -f32_rn(1.0 / 12.0);  // weight of the carried increment
   // Shared-memory rows of SE cells per line for every axis: unit stride
   // along the swept axis (window offsets are immediates); SE is odd, so the
   // y/z sweeps, whose lanes run across lines, hit distinct banks.
@@ -1570,6 +1573,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       }
       auto u0v = [&](const double* p) { return COHERENT ? __ldcg(p) : __ldg(p); };
       double up[NV], unew[NV];
+      float inc[NV];  // FP32 bulk: the increment this stage carries on
 #pragma unroll
       for (int c = 0; c < NV; ++c) {
         const long long k = perm_comp<NV>(c, dir) * A.cstride + cell;
@@ -1582,18 +1586,27 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
         const double* u0p = A.u0 + k;
         double un;
         if constexpr (FP32) {
-          // The stage's increment w dt L(u) in FP32 (L is an FP32-bulk
-          // quantity; the product rounds once more at FP32), the Shu-Osher
-          // sums in FP64: u1 = u + dt L, u2 = 3/4 u0 + (1/4 u1 + 1/4 dt L),
-          // u3 = 1/3 u0 + (2/3 u2 + 2/3 dt L) as FP64 multiply-adds -- one or
-          // two operations on the FP64 unit instead of three.
-          const double inc = f64_of(wdt32 * Lsum);
-          if (A.stage == 0)
-            un = ui + inc;
-          else if (A.stage == 1)
-            un = fma(0.75, u0v(u0p), fma(0.25, ui, inc));
-          else
-            un = fma(1.0 / 3.0, u0v(u0p), fma(2.0 / 3.0, ui, inc));
+          // Each stage as its own input u_i plus an FP32 increment, the
+          // step's increments so far carried in FP32 (each is dt times an
+          // FP32-bulk L(u)): with I0 = dt L(u0) and I1 = I0 + dt L(u1),
+          //   u1 = u0 + I0
+          //   u2 = u1 + (1/4 dt L(u1) - 3/4 I0)
+          //   u3 = u2 + (2/3 dt L(u2) - 1/12 I1),
+          // which are 3/4 u0 + 1/4 (u1 + dt L(u1)) and 1/3 u0 + 2/3 (u2 +
+          // dt L(u2)) because u1 - u0 = I0 and u2 - u0 = I1 / 4 (up to FP64
+          // rounding of u1 and u2).  One FP64 add per component (the FP64
+          // unit runs at 1/64 of the FP32 rate) and no read of U^n: the
+          // increments take the bytes U^n took, and u_i was just read by
+          // phase 1.
+          float t = wdt32 * Lsum;
+          if (A.stage > 0) {
+            const float I = COHERENT ? __ldcg(A.inc_in + k) : __ldg(A.inc_in + k);
+            inc[c] = fmaf(dt32, Lsum, I);  // I1 (stored by stage 1 only)
+            t = fmaf(inc_w, I, t);
+          } else {
+            inc[c] = t;  // I0
+          }
+          un = ui + f64_of(t);
         } else {
           const double Lk = to_f64(Lsum);
           if (A.stage == 0) {
@@ -1608,6 +1621,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       }
 #pragma unroll
       for (int c = 0; c < NV; ++c) A.u_out[perm_comp<NV>(c, dir) * A.cstride + cell] = up[c];
+      if constexpr (FP32) {
+        if (A.stage < 2) {
+#pragma unroll
+          for (int c = 0; c < NV; ++c) A.inc_out[perm_comp<NV>(c, dir) * A.cstride + cell] = inc[c];
+        }
+      }
 #pragma unroll
       for (int k = 0; k < NV; ++k) unew[k] = comp_of<NV>(up, k, dir);  // conserved order
       if constexpr (FP32) {
@@ -1968,20 +1987,24 @@ __device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo&
 
 // Adds s * dC (s = +-1/dx) to L(u) of one cell: to the stored L(u) of a
 // non-final axis, or, on the final axis, to the combined state through the
-// stage's weight of dt L (redo_coef).
+// stage's weight of dt L (redo_coef) and to the FP32 increment the stage
+// carries on (I0, I1: weight dt).
 template <int NV>
 __device__ __forceinline__ void apply_change(const SweepArgs& A, long long cell, float s,
                                              const float (&dC)[NV]) {
   const bool combine = (A.mode & kModeCombine) != 0;
   const double w = A.redo_coef * A.st->dt;
+  const float dt32 = f32_rn(A.st->dt);
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
     const long long k = perm_comp<NV>(c, A.dir) * A.cstride + cell;
     const float dL = s * dC[c];
-    if (combine)
+    if (combine) {
       A.u_out[k] += w * (double)dL;
-    else
+      if (A.inc_out) A.inc_out[k] = fmaf(dt32, dL, A.inc_out[k]);  // I0, I1 carry dt L
+    } else {
       reinterpret_cast<float*>(A.rhs)[k] += dL;
+    }
   }
 }
 
