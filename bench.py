@@ -38,7 +38,9 @@ FLOPS_PER_FACE = 1150       # flops of one face of one axis, 2D Euler ENO-AO5 (t
                             # operation count: split, Roe eigen-system, projection of both
                             # windows, indicators, selection, back-projection)
 FLOPS_PER_FACE_COUNTED = 885  # the same path counted operation by operation in the kernel
-BYTES_PER_CELL_Y = 32 + 16 + 32  # y sweep, stage 0: read U^n (FP64) and L_x (FP32), write U1 (FP64)
+# y sweep, stage 0: read U^n (FP64) and L_x (FP32), write U1 (FP64) and the
+# FP32 increment I0 the later stages combine with
+BYTES_PER_CELL_Y = 32 + 16 + 32 + 16
 WORKLOAD = "euler2d-4096x4096-quadrant-riemann-ao5"
 
 
@@ -260,7 +262,13 @@ def run_gpu(args):
         s = eno.Solver((N_CELLS, N_CELLS), (0.0, 0.0), (1.0, 1.0), stream=stream,
                        system=eno.EULER, order=5, bc=eno.TRANSMISSIVE, precision=precision)
         s.init_state(dev_U0)
-        if not args.no_autotune:
+        if args.tiles and precision == eno.FP32_BULK:
+            # the FP32-bulk tiles given on the command line (profiler captures
+            # use the ones a plain run's autotuner chose)
+            t = [int(v) for v in args.tiles.split(",")]
+            s.set_tiles(0, t[0], t[1])
+            s.set_tiles(1, t[2], t[3])
+        elif not args.no_autotune:
             s.autotune()
         s.init_state(dev_U0)
         return s
@@ -881,6 +889,8 @@ def main():
     ap.add_argument("--agree-sub", type=int, default=384)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiles", default="",
+                    help="FP32-bulk tiles x_lines,x_faces,y_lines,y_faces instead of autotuning")
     ap.add_argument("--workload", default="euler2d",
                     choices=["euler2d", "batched", "euler3d", "euler1d", "advection",
                              "tie-study", "paper-cases", "adr", "convergence", "sweep"])
