@@ -92,9 +92,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Median SM clock and the reasons seen; with t0, t1 (time.monotonic()
+        around a timed region) only the samples that arrived within it."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -104,7 +106,13 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = [ln for ts, ln in self.lines]
+        window = "whole run"
+        if t0 is not None:
+            inside = [ln for ts, ln in self.lines if t0 <= ts <= t1 + 0.15]
+            if inside:
+                lines, window = inside, "timed region"
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -118,7 +126,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def workload_state():
@@ -551,6 +559,7 @@ def run_euler3d(args):
     from paper_2108_12742_gb300 import inputs
     clk = ClockSampler(0)
     clk.start()
+    win = {}
     n = args.n3d
     U = torch.from_numpy(inputs.euler3d_blast(n, seed=1)).cuda()
     cells = n ** 3
@@ -561,7 +570,9 @@ def run_euler3d(args):
         with eno.Solver((n, n, n), (0.0,) * 3, (1.0,) * 3, stream=stream, system=eno.EULER,
                         order=7, bc=eno.PERIODIC, precision=prec) as s:
             s.init_state(U)
+            t0 = time.monotonic()
             ms = _timed_steps(s, k, 1, CFL, stream)
+            win[name] = (t0, time.monotonic())
             kms = [s.time_sweep(d, 2) for d in range(3)]
             s.init_state(U)
             s.advance_steps(1, CFL)
@@ -573,7 +584,8 @@ def run_euler3d(args):
     diff = (states["fp32_bulk"] - states["fp64"]).abs()
     l1 = [float(diff[v].mean() / states["fp64"][v].abs().mean()) for v in range(5)]
     linf = [float(diff[v].max() / states["fp64"][v].abs().max()) for v in range(5)]
-    clocks = clk.stop()
+    clocks = clk.stop(*win["fp32_bulk"])
+    out["fp64"]["clocks"] = clk.stop(*win["fp64"])
     _line(f"euler3d-{n}^3-periodic-blast-ao7", out["fp32_bulk"]["value"],
           out["fp32_bulk"]["ms_per_step"], out["fp32_bulk"]["steps"], 1,
           {"clocks": clocks, "config": {"workload": f"euler3d-{n}^3-periodic-blast-ao7", "cells": cells, "order": 7},
@@ -913,7 +925,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-subset", type=int, default=128)
     ap.add_argument("--n3d", type=int, default=512)
-    ap.add_argument("--steps3d", type=int, default=3)
+    ap.add_argument("--steps3d", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

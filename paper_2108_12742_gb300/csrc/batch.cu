@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchArgs B) {
     A.adv_speed = B.adv_speed;
     A.delta = B.delta;
     A.tie_rel = B.tie_rel;
+    set_derived_constants(A);
     A.redo_passes = 64 * NV;
 
     // alpha of the initial state of this launch

@@ -487,6 +487,7 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.adv_speed = c->cfg.adv_speed;
   a.delta = c->cfg.delta;
   a.tie_rel = c->cfg.tie_rel;
+  set_derived_constants(a);
   a.redo_passes = c->redo_passes >= 0 ? c->redo_passes : 64 * c->nv;
   CUtensorMap tmap;
   const size_t smem0 = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts, a.se);

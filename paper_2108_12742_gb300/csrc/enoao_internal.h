@@ -108,7 +108,23 @@ struct SweepArgs {
   double adv_speed;
   double delta;
   double tie_rel;
+  // gamma - 1 in FP64 and the constants in FP32 (FP32 bulk), set from the
+  // fields above by set_derived_constants wherever they are set: kernels read
+  // them from the parameter space instead of narrowing them themselves, which
+  // the compiler may redo at every use (a conversion on the FP64 unit each).
+  double gm1;
+  float gm1_f, adv_f, delta_f, tie_rel_f, inv_dx_f;
 };
+
+// Derived constants of a SweepArgs (round to nearest, as the device would).
+__host__ __device__ inline void set_derived_constants(SweepArgs& a) {
+  a.gm1 = a.gamma - 1.0;
+  a.gm1_f = (float)a.gm1;
+  a.adv_f = (float)a.adv_speed;
+  a.delta_f = (float)a.delta;
+  a.tie_rel_f = (float)a.tie_rel;
+  a.inv_dx_f = (float)a.inv_dx;
+}
 
 // Host-side entry points of the instantiation units (sweep_fp64.cu,
 // sweep_fp32.cu); return cudaError_t values.

@@ -200,6 +200,7 @@ extern "C" enoao_status enoao_step_noalloc(const enoao_config* cfg, const double
   a.adv_speed = cfg->adv_speed;
   a.delta = cfg->delta;
   a.tie_rel = cfg->tie_rel;
+  set_derived_constants(a);
   a.redo_passes = 64 * nv;
   const size_t smem = sweep_smem_bytes(nv, cfg->order, f32, a.ta, a.ts, a.se);
   const int block = 128;

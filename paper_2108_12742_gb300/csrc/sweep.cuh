@@ -145,6 +145,14 @@ template <>
 __device__ __forceinline__ float to_bulk<float>(double x) { return f32_near(x); }
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f64_of(x); }
+// A constant of the sweep in the bulk precision: the FP64 argument, or its
+// FP32 copy set on the host (SweepArgs, set_derived_constants).
+template <typename R>
+__device__ __forceinline__ R bconst(double d, float f);
+template <>
+__device__ __forceinline__ double bconst<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float bconst<float>(double, float f) { return f; }
 
 // ENO-AO choice on one window of first differences d[LO..HI] (d[i] between
 // offsets i-4 and i-3 of the centre cell).  Returns f^ - f_centre.  When
@@ -601,7 +609,7 @@ __device__ __forceinline__ int redo_group(const SweepArgs& A, const TileGeo& g, 
   constexpr int G = Geo<ORDER>::G;
   static_assert(W >= 2 * G, "a lane per window cell");
   const unsigned FULL = 0xffffffffu;
-  const double gm1 = A.gamma - 1.0;
+  const double gm1 = A.gm1;
   const long long line = g.base + (g.a0 + a) * g.stride_a;
   const int rr = r < 2 * G ? r : 2 * G - 1;
   double q[NV];
@@ -662,7 +670,7 @@ __device__ __forceinline__ int redo_lane(const SweepArgs& A, const TileGeo& g, i
                                          int v, int sgn, double alpha) {
   using GE = Geo<ORDER>;
   constexpr int G = GE::G;
-  const double gm1 = A.gamma - 1.0;
+  const double gm1 = A.gm1;
   const long long line = g.base + (g.a0 + a) * g.stride_a;
   // window cell r (0..2G-1) is cell sj - G + 1 + r of the line; the face lies
   // between cells G-1 and G
@@ -1091,9 +1099,9 @@ __device__ __forceinline__ void redecide_tile(const SweepArgs& A, const TileGeo&
   const int lgTA = __ffs(TA) - 1;
   const int nts = g.nts;
   const int mode = A.mode;
-  const R gm1 = (R)(A.gamma - 1.0);
-  const R delta = (R)A.delta;
-  const R tie_rel = (R)A.tie_rel;
+  const R gm1 = bconst<R>(A.gm1, A.gm1_f);
+  const R delta = bconst<R>(A.delta, A.delta_f);
+  const R tie_rel = bconst<R>(A.tie_rel, A.tie_rel_f);
   const R alpha = (R)alpha_d;
   R alo = alpha, amid = alpha, ahi = alpha;
   if constexpr (FIELD) {
@@ -1307,14 +1315,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
     if constexpr (FIELD) return field_alpha<NV>(st, A.dir, v);
     return alpha_d;
   };
-  const R gm1 = (R)(A.gamma - 1.0);
-  const R adv = (R)A.adv_speed;
-  const R delta = (R)A.delta;
-  const R tie_rel = (R)A.tie_rel;
+  const R gm1 = bconst<R>(A.gm1, A.gm1_f);
+  const R adv = bconst<R>(A.adv_speed, A.adv_f);
+  const R delta = bconst<R>(A.delta, A.delta_f);
+  const R tie_rel = bconst<R>(A.tie_rel, A.tie_rel_f);
   const int mode = A.mode;
   const double inv_dx = A.inv_dx;
-  const R inv_dx_r = (R)inv_dx;
-  // FP32 bulk combine: the stage's weight of dt L(u) (1, 1/4, 2/3) times dt
+  const R inv_dx_r = bconst<R>(inv_dx, A.inv_dx_f);
   // FP32 bulk combine: dt and the stage's weight of dt L in FP32
   const float dt32 = f32_rn(dt);
   const float wdt32 = f32_rn((A.stage == 0 ? 1.0 : (A.stage == 1 ? 0.25 : 2.0 / 3.0)) * dt);
@@ -1519,8 +1526,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
       double ql[NV], qr[NV], Fl[NV], Fr[NV];
       load_state<NV, COHERENT>(A.u_in, A.cstride, la + bc_map(gface - 1, g.nd, A.bc) * g.stride_d, dir, ql);
       load_state<NV, COHERENT>(A.u_in, A.cstride, la + bc_map(gface, g.nd, A.bc) * g.stride_d, dir, qr);
-      phys_flux<NV>(ql, A.gamma - 1.0, A.adv_speed, Fl);
-      phys_flux<NV>(qr, A.gamma - 1.0, A.adv_speed, Fr);
+      phys_flux<NV>(ql, A.gm1, A.adv_speed, Fl);
+      phys_flux<NV>(qr, A.gm1, A.adv_speed, Fr);
       const long long fc = g.fbase + (g.a0 + a) * g.fstride_a + gface * g.fstride_d;
       R Cv[NV];
       CV::load(Cf, cells, sidx(a, j), Cv);
@@ -1904,7 +1911,7 @@ __device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo&
                                               int v, int sgn, int pick64, double alpha_d,
                                               float (&dC)[NV], bool& changed) {
   using GE = Geo<ORDER>;
-  const float gm1 = (float)(A.gamma - 1.0), adv = (float)A.adv_speed;
+  const float gm1 = A.gm1_f, adv = A.adv_f;
   const float halpha = 0.5f * (float)alpha_d;
   auto cell = [&](long long gi, double (&q)[NV]) {
     load_state<NV, false>(A.u_in, A.cstride, g.base + bc_map(gi, g.nd, A.bc) * g.stride_d, A.dir, q);
@@ -1965,7 +1972,7 @@ __device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo&
   int pick32;
   bool m;
   const float nomx[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  const float corr_old = eno_select<ORDER, float, false>(d, (float)A.delta, (float)A.tie_rel, nomx,
+  const float corr_old = eno_select<ORDER, float, false>(d, A.delta_f, A.tie_rel_f, nomx,
                                                          0.0f, pick32, m);
   if (pick64 == pick32) return;
   changed = true;
@@ -2025,7 +2032,7 @@ __global__ void __launch_bounds__(128) redo_kernel(const SweepArgs A) {
   const unsigned n = st->redo_n < A.redo_cap ? st->redo_n : (unsigned)A.redo_cap;
   const unsigned epoch = st->redo_epoch;
   const double alpha_d = st->alpha[A.dir];
-  const float inv_dx = (float)A.inv_dx;
+  const float inv_dx = A.inv_dx_f;
   const int lane = threadIdx.x & 31;
   const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
   unsigned long long nf = 0;
@@ -2121,7 +2128,7 @@ __global__ void __launch_bounds__(128) redo_apply_kernel(const SweepArgs A) {
   StepState* st = A.st;
   const unsigned n = st->skip ? 0u : (st->redo_n < A.redo_cap ? st->redo_n : (unsigned)A.redo_cap);
   const unsigned epoch = st->redo_epoch;
-  const float inv_dx = (float)A.inv_dx;
+  const float inv_dx = A.inv_dx_f;
   const bool check = (A.mode & kModeCombine) != 0;
   double amax[3] = {0.0, 0.0, 0.0};
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

@@ -185,6 +185,21 @@ def test_constant_state_gives_identical_fluxes(name):
     assert np.abs(got - const).max() <= 8 * np.spacing(np.abs(const).max())
 
 
+@pytest.mark.parametrize("shape", [(200,), (64, 48)])
+def test_fp32_bulk_constant_state_stays_exact(shape):
+    # L(u) of a constant state is zero bit for bit, and the FP32-bulk stages
+    # add their increments to each stage's own input: the state never changes
+    q = np.array([1.3, -0.4, 0.7, 2.9]) if len(shape) == 2 else np.array([1.3, -0.4, 2.9])
+    const = np.ascontiguousarray(
+        np.broadcast_to(q.reshape(-1, 1, 1, 1), (len(q), 1) + (1,) * (2 - len(shape)) + shape[::-1]))
+    with eno.Solver(shape, (0.0,) * len(shape), (1.0,) * len(shape), system=eno.EULER, order=5,
+                    precision=eno.FP32_BULK) as s:
+        s.init_state(const)
+        s.advance(1e9, cfl=0.5, max_steps=3)
+        got = s.get_state()
+    assert np.array_equal(got.reshape(const.shape), const)
+
+
 def test_full_c2_run_per_step_samples():
     # the 1D Euler workload at its full size (N = 2000, t_end = 0.2): run on the
     # GPU, and at sampled steps re-do that step in the oracle from the GPU state
