@@ -763,6 +763,22 @@ __device__ __forceinline__ void for_items(int lgTA, int cnt, bool sfast, F&& bod
   }
 }
 
+// The mapping of for_items as values: this thread's line a, its first item
+// e0 and the stride between its items.
+__device__ __forceinline__ void item_start(int lgTA, bool sfast, int& a, int& e0, int& step) {
+  const int bd = blockDim.x, tid = threadIdx.x;
+  if (sfast) {
+    const int lgTpl = __ffs(bd) - 1 - lgTA;
+    a = tid >> lgTpl;
+    step = 1 << lgTpl;
+    e0 = tid & (step - 1);
+  } else {
+    a = tid & ((1 << lgTA) - 1);
+    step = bd >> lgTA;
+    e0 = tid >> lgTA;
+  }
+}
+
 // Per-cell vectors in shared memory.  FP32 four-component states (2D Euler)
 // are stored as one float4 per cell, so a cell moves in one 128-bit access;
 // every other case keeps one plane per component.  Both layouts take NV
@@ -795,14 +811,11 @@ struct CellVec {
 // dF/2 +- (alpha/2) dq (the same bits: halving is exact).
 template <int NV, typename R>
 __device__ __forceinline__ void split_diff(const double (&qa64)[NV], const double (&qb64)[NV],
-                                           const R (&qa)[NV], R gm1, R adv, R halpha,
-                                           R (&fp)[NV], R (&fm)[NV]) {
-  R qb[NV], dq[NV], dF[NV];
+                                           const R (&qa)[NV], const R (&qb)[NV], R gm1, R adv,
+                                           R halpha, R (&fp)[NV], R (&fm)[NV]) {
+  R dq[NV], dF[NV];
 #pragma unroll
-  for (int c = 0; c < NV; ++c) {
-    qb[c] = to_bulk<R>(qb64[c]);
-    dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
-  }
+  for (int c = 0; c < NV; ++c) dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
   flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
@@ -816,14 +829,11 @@ __device__ __forceinline__ void split_diff(const double (&qa64)[NV], const doubl
 // halvings), to be split per characteristic field after the projection.
 template <int NV, typename R>
 __device__ __forceinline__ void split_parts(const double (&qa64)[NV], const double (&qb64)[NV],
-                                            const R (&qa)[NV], R gm1, R adv, R (&hdF)[NV],
-                                            R (&hdq)[NV]) {
-  R qb[NV], dq[NV], dF[NV];
+                                            const R (&qa)[NV], const R (&qb)[NV], R gm1, R adv,
+                                            R (&hdF)[NV], R (&hdq)[NV]) {
+  R dq[NV], dF[NV];
 #pragma unroll
-  for (int c = 0; c < NV; ++c) {
-    qb[c] = to_bulk<R>(qb64[c]);
-    dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
-  }
+  for (int c = 0; c < NV; ++c) dq[c] = to_bulk<R>(qb64[c] - qa64[c]);
   flux_diff<NV, R>(qa, qb, dq, gm1, adv, dF);
 #pragma unroll
   for (int c = 0; c < NV; ++c) {
@@ -1344,45 +1354,91 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
   // ---------------- phase 1: split differences and Roe ingredients
   {
     const int cnt = sext;
-    for_items(lgTA, cnt, sfast, [&](const int a, const int e) {
-      if (g.a0 + a >= g.na) return;
-      const long long la = g.base + (g.a0 + a) * g.stride_a;
-      double qa64[NV];
-      // the tile's raw state: staged by TMA, or straight from global memory
-      auto cell_state = [&](int ee, double (&q)[NV]) {
-        if constexpr (TMA) {
-          const double* p = rt.p + a * rt.ra + (ee + rt.xoff) * rt.re;
+    // the tile's raw state: staged by TMA, or straight from global memory
+    auto cell_state = [&](int a, int ee, double (&q)[NV]) {
+      if constexpr (TMA) {
+        const double* p = rt.p + a * rt.ra + (ee + rt.xoff) * rt.re;
 #pragma unroll
-          for (int c = 0; c < NV; ++c) q[c] = p[perm_comp<NV>(c, dir) * rt.rc];
-        } else {
-          load_state<NV, COHERENT>(A.u_in, A.cstride,
-                                   la + bc_map(g.s0 - G + ee, g.nd, A.bc) * g.stride_d, dir, q);
-        }
-      };
-      cell_state(e, qa64);
-      R qa[NV];
-#pragma unroll
-      for (int c = 0; c < NV; ++c) qa[c] = to_bulk<R>(qa64[c]);
-      const int si = sidx(a, e);
+        for (int c = 0; c < NV; ++c) q[c] = p[perm_comp<NV>(c, dir) * rt.rc];
+      } else {
+        const long long la = g.base + (g.a0 + a) * g.stride_a;
+        load_state<NV, COHERENT>(A.u_in, A.cstride,
+                                 la + bc_map(g.s0 - G + ee, g.nd, A.bc) * g.stride_d, dir, q);
+      }
+    };
+    // cell e's Roe ingredients, and the split differences of the pair (e, e+1)
+    auto prim_out = [&](int a, int e, const R (&qa)[NV]) {
       if constexpr (NP > 0) {
         if (e >= G - 1 && e <= G + nts) {
           R pr[NV];
           roe_prims<NV, R>(qa, gm1, pr);
-          CV::store(prim, cells, si, pr);
+          CV::store(prim, cells, sidx(a, e), pr);
         }
       }
-      if (e + 1 < cnt) {
-        double qb64[NV];
-        cell_state(e + 1, qb64);
-        R fp[NV], fm[NV];
-        if constexpr (FIELD)
-          split_parts<NV, R>(qa64, qb64, qa, gm1, adv, fp, fm);  // dF/2, dq/2
-        else
-          split_diff<NV, R>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
-        CV::store(dfp, cells, si, fp);
-        CV::store(dfm, cells, si, fm);
+    };
+    auto pair_out = [&](int a, int e, const double (&qa64)[NV], const R (&qa)[NV],
+                        const double (&qb64)[NV], const R (&qb)[NV]) {
+      R fp[NV], fm[NV];
+      if constexpr (FIELD)
+        split_parts<NV, R>(qa64, qb64, qa, qb, gm1, adv, fp, fm);  // dF/2, dq/2
+      else
+        split_diff<NV, R>(qa64, qb64, qa, qb, gm1, adv, halpha, fp, fm);
+      CV::store(dfp, cells, sidx(a, e), fp);
+      CV::store(dfm, cells, sidx(a, e), fm);
+    };
+    if (sfast) {
+      // x sweeps: lanes along the line (coalesced), one pair per item
+      for_items(lgTA, cnt, sfast, [&](const int a, const int e) {
+        if (g.a0 + a >= g.na) return;
+        double qa64[NV];
+        cell_state(a, e, qa64);
+        R qa[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) qa[c] = to_bulk<R>(qa64[c]);
+        prim_out(a, e, qa);
+        if (e + 1 < cnt) {
+          double qb64[NV];
+          cell_state(a, e + 1, qb64);
+          R qb[NV];
+#pragma unroll
+          for (int c = 0; c < NV; ++c) qb[c] = to_bulk<R>(qb64[c]);
+          pair_out(a, e, qa64, qa, qb64, qb);
+        }
+      });
+    } else {
+      // y/z sweeps: lanes across lines, so a thread can take a run of
+      // consecutive cells of its line without losing coalescing; each cell
+      // is then loaded and narrowed once (the right cell of one pair is the
+      // left cell of the next), the run's last pair reaching one cell on
+      int a, j0, step;
+      item_start(lgTA, false, a, j0, step);
+      const int run = (cnt + step - 1) / step;
+      int e = j0 * run;
+      const int e_end = min(e + run, cnt);
+      if (g.a0 + a < g.na && e < e_end) {
+        double q64[NV];
+        cell_state(a, e, q64);
+        R q[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) q[c] = to_bulk<R>(q64[c]);
+        for (;; ++e) {
+          prim_out(a, e, q);
+          if (e + 1 >= cnt) break;
+          double n64[NV];
+          cell_state(a, e + 1, n64);
+          R n[NV];
+#pragma unroll
+          for (int c = 0; c < NV; ++c) n[c] = to_bulk<R>(n64[c]);
+          pair_out(a, e, q64, q, n64, n);
+          if (e + 1 >= e_end) break;
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            q64[c] = n64[c];
+            q[c] = n[c];
+          }
+        }
       }
-    });
+    }
   }
   __syncthreads();
   hook();
@@ -1949,10 +2005,13 @@ __device__ __forceinline__ void face_change32(const SweepArgs& A, const TileGeo&
     double qa64[NV], qb64[NV];
     cell(c0, qa64);
     cell(c0 + 1, qb64);
-    float qa[NV], fp[NV], fm[NV], x[NV];
+    float qa[NV], qb[NV], fp[NV], fm[NV], x[NV];
 #pragma unroll
-    for (int c = 0; c < NV; ++c) qa[c] = to_bulk<float>(qa64[c]);
-    split_diff<NV, float>(qa64, qb64, qa, gm1, adv, halpha, fp, fm);
+    for (int c = 0; c < NV; ++c) {
+      qa[c] = to_bulk<float>(qa64[c]);
+      qb[c] = to_bulk<float>(qb64[c]);
+    }
+    split_diff<NV, float>(qa64, qb64, qa, qb, gm1, adv, halpha, fp, fm);
 #pragma unroll
     for (int c = 0; c < NV; ++c) x[c] = sgn == 0 ? fp[c] : fm[c];
     float acc = 0.0f;
