@@ -222,7 +222,10 @@ enoao_status enoao_get_stage_state(enoao_ctx *ctx, int k, double *U, int on_devi
  * S_{j-1}^{j+1}, S_{j-2}^{j+1}, S_{j-1}^{j+2}, S_{j-2}^{j+2}, S_{j-3}^{j+2},
  * S_{j-2}^{j+3}, S_{j-3}^{j+3}) per characteristic field v (Euler order:
  * u-c, entropy, shear..., u+c), sign s (0: f^+, 1: f^-) and face at
- * stencil_idx[(v*2 + s)*nfaces + face].  Not available for batched contexts. */
+ * stencil_idx[(v*2 + s)*nfaces + face].  Not available for batched contexts.
+ * With host buffers (on_device = 0) the results pass through device scratch
+ * that the context keeps: the first call (or one that needs more of it)
+ * allocates it, enoao_destroy frees it. */
 enoao_status enoao_reconstruct_fluxes(enoao_ctx *ctx, int dir, double *Fhat,
                                       int8_t *stencil_idx, int on_device);
 
@@ -231,7 +234,11 @@ enoao_status enoao_reconstruct_fluxes(enoao_ctx *ctx, int dir, double *Fhat,
  *   stage 1: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1))
  *   stage 2: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2))
  * Stages must be called in order; after stage 2 the state is U^{n+1} and the
- * step count and time advance by one step and dt. */
+ * step count and time advance by one step and dt.  In FP32 bulk the stages
+ * are evaluated as each stage's input plus an FP32 increment (U2 = U1 +
+ * 1/4 dt L(U1) - 3/4 I0, U^{n+1} = U2 + 2/3 dt L(U2) - 1/12 I1, with I0 =
+ * dt L(U^n) and I1 = I0 + dt L(U1) kept by the context), equal to the forms
+ * above up to an FP32 rounding of the increment. */
 enoao_status enoao_rk_stage(enoao_ctx *ctx, int stage, double dt);
 
 /* Advances to t_end with dt = cfl / sum_d(alpha_d / dx_d), alpha from U^n of

@@ -949,6 +949,8 @@ void enoao_destroy(enoao_ctx* c) {
   for (int k = 0; k < 3; ++k) cudaFree(c->U[k]);
   cudaFree(c->rhs);
   for (int k = 0; k < 2; ++k) cudaFree(c->inc[k]);
+  cudaFree(c->flux_scratch);
+  cudaFree(c->idx_scratch);
   cudaFree(c->redo);
   cudaFree(c->redo_dc);
   cudaFree(c->redo_mark);
@@ -1021,14 +1023,30 @@ enoao_status enoao_reconstruct_fluxes(enoao_ctx* c, int dir, double* Fhat, int8_
   double* dF = Fhat;
   int8_t* dI = idx;
   if (!on_device) {
-    CU(c, cudaMalloc(&dF, fbytes));
-    if (idx) {
-      cudaError_t e = cudaMalloc(&dI, ibytes);
-      if (e != cudaSuccess) {
-        cudaFree(dF);
-        return fail(c, ENOAO_ENOMEM, "scratch allocation failed");
+    // device scratch kept in the context: allocated by the first call that
+    // needs it (or more of it), freed by enoao_destroy
+    if (c->flux_scratch_bytes < fbytes) {
+      cudaFree(c->flux_scratch);
+      c->flux_scratch = nullptr;
+      c->flux_scratch_bytes = 0;
+      if (cudaMalloc(&c->flux_scratch, fbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ENOAO_ENOMEM, "flux scratch allocation of %zu bytes failed", fbytes);
       }
+      c->flux_scratch_bytes = fbytes;
     }
+    if (idx && c->idx_scratch_bytes < ibytes) {
+      cudaFree(c->idx_scratch);
+      c->idx_scratch = nullptr;
+      c->idx_scratch_bytes = 0;
+      if (cudaMalloc(&c->idx_scratch, ibytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, ENOAO_ENOMEM, "choice scratch allocation of %zu bytes failed", ibytes);
+      }
+      c->idx_scratch_bytes = ibytes;
+    }
+    dF = c->flux_scratch;
+    dI = idx ? c->idx_scratch : nullptr;
   }
   enoao_status r = enter(c);
   if (r == ENOAO_OK) {
@@ -1042,10 +1060,6 @@ enoao_status enoao_reconstruct_fluxes(enoao_ctx* c, int dir, double* Fhat, int8_
   }
   if (r == ENOAO_OK) r = leave(c);
   cudaError_t e = cudaStreamSynchronize(c->s);
-  if (!on_device) {
-    cudaFree(dF);
-    if (idx) cudaFree(dI);
-  }
   if (r != ENOAO_OK) return r;
   if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "reconstruct_fluxes: %s", cudaGetErrorString(e));
   return ENOAO_OK;

@@ -31,6 +31,11 @@ struct enoao_ctx {
   double* U[3] = {nullptr, nullptr, nullptr};  // U^n, U1, U2
   void* rhs = nullptr;
   float* inc[2] = {nullptr, nullptr};  // FP32 bulk: stage increments I0, I1 ([nv][carr])
+  // device scratch of enoao_reconstruct_fluxes with host buffers (grown on demand)
+  double* flux_scratch = nullptr;
+  size_t flux_scratch_bytes = 0;
+  int8_t* idx_scratch = nullptr;
+  size_t idx_scratch_bytes = 0;
   enoao::StepState* st = nullptr;       // device
   enoao::StepState* st_host = nullptr;  // pinned mirror
   int ta[3] = {0, 0, 0}, ts[3] = {0, 0, 0}, block[3] = {128, 128, 128};
