@@ -179,6 +179,23 @@ def measure_peaks(local):
     return out
 
 
+def step_roofline(value, flops_per_cs, bytes_fused, bytes_split, peaks, hbm):
+    """Whole-step roofline of a workload line: the method's flops per
+    cell-stage (§8(d)'s count) times the line's cell-stage rate against the
+    FP32 multiply-add peak measured in this run, and the bytes per cell-stage
+    of an all-axes-fused design and of this per-axis design against the
+    measured copy bandwidth."""
+    achieved = flops_per_cs * value / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peaks["fp32"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["fp32"], "traffic": None,
+            "flops_per_cell_stage": flops_per_cs, "kind": "whole step (every sweep of a stage)",
+            "peak_kind": "measured: FP32 multiply-add microbenchmark on this GPU, 'of measured'",
+            "hbm": {"peak": hbm, "unit": "GB/s",
+                    "frac_fused_bytes": bytes_fused * value / 1e9 / hbm,
+                    "frac_per_axis_bytes": bytes_split * value / 1e9 / hbm,
+                    "bytes_per_cell_stage": {"fused": bytes_fused, "per_axis": bytes_split}}}
+
+
 def profiled_traffic(summary):
     """DRAM bytes per launch of the dominant kernel at 4096^2, from the committed
     ncu summary, if that summary was taken on the current kernel source."""
@@ -539,12 +556,15 @@ def run_batched(args):
     a, b = res["fp32_bulk"]["state"], res["fp64"]["state"]
     l1 = [float(np.abs(a[v] - b[v]).mean() / np.abs(b[v]).mean()) for v in range(3)]
     clocks = clk.stop()
+    mp, _ = measured_peaks()
+    roof = step_roofline(res["fp32_bulk"]["value"], 760, 64, 64, measure_peaks(0), mp["hbm_gbs"])
     _line("batched-euler1d-4096-problems-N256-16384-ao5", res["fp32_bulk"]["value"],
           res["fp32_bulk"]["ms_total"] / nsteps, nsteps, 1,
           {"clocks": clocks, "config": {"workload": "batched-euler1d-4096-problems-N256-16384-ao5", "cells": cells,
                       "problems": nprob, "steps_per_launch": nsteps, "launches": 1},
            "fp64": {"value": res["fp64"]["value"], "ms_total": res["fp64"]["ms_total"]},
            "fp32_bulk_speedup_vs_fp64": res["fp32_bulk"]["value"] / res["fp64"]["value"],
+           "roofline": roof,
            "one_launch_per_problem": {"value": per_problem, "problems_timed": len(sub),
                                       "cells_timed": cells_sub,
                                       "note": "single-problem path, FP32 bulk, same steps"},
@@ -590,11 +610,14 @@ def run_euler3d(args):
     linf = [float(diff[v].max() / states["fp64"][v].abs().max()) for v in range(5)]
     clocks = clk.stop(*win["fp32_bulk"])
     out["fp64"]["clocks"] = clk.stop(*win["fp64"])
+    peaks_run = measure_peaks(0)
+    mp, _ = measured_peaks()
+    roof = step_roofline(out["fp32_bulk"]["value"], 6000, 107, 347, peaks_run, mp["hbm_gbs"])
     _line(f"euler3d-{n}^3-periodic-blast-ao7", out["fp32_bulk"]["value"],
           out["fp32_bulk"]["ms_per_step"], out["fp32_bulk"]["steps"], 3,
           {"clocks": clocks, "config": {"workload": f"euler3d-{n}^3-periodic-blast-ao7", "cells": cells, "order": 7},
            "fp64": out["fp64"], "kernel_ms_fp32_bulk": out["fp32_bulk"]["kernel_ms"],
-           "tiles_fp32_bulk": out["fp32_bulk"].get("tiles"),
+           "tiles_fp32_bulk": out["fp32_bulk"].get("tiles"), "roofline": roof,
            "fp32_bulk_speedup_vs_fp64": out["fp32_bulk"]["value"] / out["fp64"]["value"],
            "l1_rel_fp32_bulk_vs_fp64_one_step": l1, "linf_rel_fp32_bulk_vs_fp64_one_step": linf})
 
