@@ -309,6 +309,22 @@ int enoao_uses_grid_redecide(const enoao_ctx *ctx);
  * The results are the same bits. */
 enoao_status enoao_set_tma(enoao_ctx *ctx, int on);
 
+/* Whether each Runge-Kutta stage of a 2D problem runs as one launch for both
+ * axes (on = 1; Sec. 2: L(u) is the unsplit sum of the two axes' flux
+ * differences) instead of one launch per axis (0, the default).  A block
+ * takes a 2D tile of x_cells x y_cells cells: the x part of L(u) on it in
+ * tiles of x_lines rows x x_cells cells, then the y part in tiles of y_lines
+ * columns x y_cells cells, which adds the x part the block just stored and
+ * combines.  x_lines: 1, 2, 4 or 8; y_lines: 8, 16, 32 or 64; y_cells a
+ * multiple of x_lines and x_cells of y_lines; all four 0 keeps the current
+ * tiles (4, 64, 8, 48 by default).  It applies to FP32-bulk contexts with one
+ * alpha and in-sweep re-decisions, without TMA staging, of 2D scalar
+ * advection or Euler, ENO-AO5 or AO7, on a whole grid; other contexts keep
+ * one launch per axis.  The results are the same bits either way.
+ * ENOAO_EINVAL for a 3D or 1D context, bad tiles or a batched context. */
+enoao_status enoao_set_fused_stage(enoao_ctx *ctx, int on, int x_lines, int x_cells, int y_lines,
+                                   int y_cells);
+
 /* Fault-injection knob for tests (the paper has no counterpart): bounds the
  * passes in which a warp re-decides its flagged FP32-bulk choices inside the
  * sweep (the default, -1, is 64 nv passes, which every warp needs at most

@@ -108,6 +108,8 @@ def load():
         "enoao_uses_grid_redecide": (ctypes.c_int, [P]),
         "enoao_set_redecide_pass_limit": (ctypes.c_int, [P, ctypes.c_int]),
         "enoao_set_tma": (ctypes.c_int, [P, ctypes.c_int]),
+        "enoao_set_fused_stage": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int]),
         "enoao_get_tiles": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]),
         "enoao_autotune": (ctypes.c_int, [P]),
@@ -324,8 +326,14 @@ class Solver:
         self._check(self._lib.enoao_set_redecide(self._h, mode))
 
     def set_tma(self, on):
-        """FP32 bulk: stage raw tiles by TMA (True, default) or load them directly."""
+        """FP32 bulk: stage raw tiles by TMA (True) or load them directly (False, default)."""
         self._check(self._lib.enoao_set_tma(self._h, 1 if on else 0))
+
+    def set_fused_stage(self, on, tiles=(0, 0, 0, 0)):
+        """2D: one launch per Runge-Kutta stage for both axes (True) or one per
+        axis (False, default); tiles = (x_lines, x_cells, y_lines, y_cells), all
+        0 to keep the current ones."""
+        self._check(self._lib.enoao_set_fused_stage(self._h, 1 if on else 0, *[int(t) for t in tiles]))
 
     def set_redecide_pass_limit(self, passes):
         """Test knob: bound on the in-sweep FP64 re-decision passes (-1: default)."""

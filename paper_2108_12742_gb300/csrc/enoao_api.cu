@@ -432,10 +432,10 @@ bool encode_tile_map(enoao_ctx* c, int d, bool list, const double* u_in, SweepAr
 // list: a stepping sweep (stage 0..2) of a context that uses the re-decision
 // list; the pass is launched right after the sweep (after recording
 // after_sweep, when given).
-enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double* u_in,
-                          double* u_out, double* fhat, int8_t* idx, bool list = false,
-                          cudaEvent_t after_sweep = nullptr) {
-  SweepArgs a;
+// The arguments of a sweep of axis d with tiles of ta lines x ts cells.
+enoao_status fill_sweep_args(enoao_ctx* c, int d, int stage, int mode, const double* u_in,
+                             double* u_out, double* fhat, int8_t* idx, bool list, int ta, int ts,
+                             SweepArgs& a) {
   memset(&a, 0, sizeof a);
   if (list) {
     a.redo = c->redo;
@@ -466,8 +466,8 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.bc = c->sub && d == c->cfg.ndim - 1 ? kBcHalo : c->cfg.bc[d];
   a.mode = mode;
   a.stage = stage;
-  a.ta = c->ta[d];
-  a.ts = c->ts[d];
+  a.ta = ta;
+  a.ts = ts;
   a.se = sweep_row_pitch(c->nv, c->cfg.order, fp32(c), d, a.ta, a.ts);
   const long long nd = c->cfg.n[d];
   a.nfaces = c->ncell / nd * (nd + 1);
@@ -489,6 +489,16 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   a.tie_rel = c->cfg.tie_rel;
   set_derived_constants(a);
   a.redo_passes = c->redo_passes >= 0 ? c->redo_passes : 64 * c->nv;
+  return ENOAO_OK;
+}
+
+enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double* u_in,
+                          double* u_out, double* fhat, int8_t* idx, bool list = false,
+                          cudaEvent_t after_sweep = nullptr) {
+  SweepArgs a;
+  enoao_status r0 = fill_sweep_args(c, d, stage, mode, u_in, u_out, fhat, idx, list, c->ta[d],
+                                    c->ts[d], a);
+  if (r0 != ENOAO_OK) return r0;
   CUtensorMap tmap;
   const size_t smem0 = sweep_smem_bytes(c->nv, c->cfg.order, fp32(c), a.ta, a.ts, a.se);
   bool tma = encode_tile_map(c, d, list, u_in, a, &tmap);
@@ -547,6 +557,52 @@ bool per_stage_alpha(const enoao_ctx* c) {
   return c->cfg.system == ENOAO_EULER && c->cfg.alpha_mode == ENOAO_ALPHA_PER_STAGE;
 }
 
+// Whether a stage of this context runs as one fused 2D launch: asked for,
+// 2D, FP32 bulk, one alpha, in-sweep re-decisions, no TMA staging, a whole
+// grid (not a sub-domain), and a system the fused kernel is built for.
+bool fused_stage(const enoao_ctx* c) {
+  return c->fused && c->cfg.ndim == 2 && fp32(c) && !use_list(c) && !consts(c).field && !c->tma &&
+         !c->sub && (c->nv == 1 || c->nv == 4) && (c->cfg.order == 5 || c->cfg.order == 7);
+}
+
+// One stage as one launch of fused2d_kernel: the x part with tiles of
+// fused_tiles[0] rows x fused_tiles[1] cells, the y part with tiles of
+// fused_tiles[2] columns x fused_tiles[3] cells, on 2D tiles of
+// fused_tiles[1] x fused_tiles[3] cells.
+enoao_status launch_fused_stage(enoao_ctx* c, int stage, const double* in, double* out,
+                                bool want_alpha) {
+  const int* ft = c->fused_tiles;
+  SweepArgs ax, ay;
+  enoao_status r = fill_sweep_args(c, 0, stage, kModeRhsStore, in, out, nullptr, nullptr, false,
+                                   ft[0], ft[1], ax);
+  if (r != ENOAO_OK) return r;
+  r = fill_sweep_args(c, 1, stage, kModeCombine | kModeRhsAdd | (want_alpha ? kModeAlpha : 0), in,
+                      out, nullptr, nullptr, false, ft[2], ft[3], ay);
+  if (r != ENOAO_OK) return r;
+  const int nv = c->nv, order = c->cfg.order, block = 128;
+  const size_t sx = sweep_smem_bytes(nv, order, true, ax.ta, ax.ts, ax.se);
+  const size_t sy = sweep_smem_bytes(nv, order, true, ay.ta, ay.ts, ay.se);
+  const size_t smem = sx > sy ? sx : sy;
+  int lean = 0, per_sm = 0;
+  if (order == 5 && smem * 7 <= 220 * 1024) {
+    int p = 0;
+    if (fused2d_configure_fp32(nv, order, smem, 1) == cudaSuccess &&
+        fused2d_occupancy_fp32(nv, order, block, smem, &p, 1) == cudaSuccess && p >= 7)
+      lean = 1;
+    cudaGetLastError();
+  }
+  cudaError_t e = fused2d_configure_fp32(nv, order, smem, lean);
+  if (e == cudaSuccess) e = fused2d_occupancy_fp32(nv, order, block, smem, &per_sm, lean);
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "fused stage setup: %s", cudaGetErrorString(e));
+  if (per_sm < 1) return fail(c, ENOAO_EINVAL, "fused stage tiles do not fit on an SM");
+  const long long tiles = ax.tiles_s * ay.tiles_s;
+  long long grid = std::min<long long>(tiles, (long long)c->sms * per_sm);
+  if (grid < 1) grid = 1;
+  e = fused2d_launch_fp32(nv, order, ax, ay, (int)grid, block, smem, c->s, lean);
+  if (e != cudaSuccess) return fail(c, ENOAO_ECUDA, "fused stage launch: %s", cudaGetErrorString(e));
+  return ENOAO_OK;
+}
+
 enoao_status enqueue_stage(enoao_ctx* c, int stage) {
   const double* in = c->U[stage];                 // U^n, U1, U2
   double* out = c->U[stage == 2 ? 0 : stage + 1];  // U1, U2, U^{n+1}
@@ -558,6 +614,7 @@ enoao_status enqueue_stage(enoao_ctx* c, int stage) {
   // alpha of the written state: for the next step (stage 2), or for the next
   // stage when each stage takes its own
   const bool want_alpha = stage == 2 || per_stage_alpha(c);
+  if (fused_stage(c)) return launch_fused_stage(c, stage, in, out, want_alpha);
   const bool list = use_list(c);
   if (list && !c->redo) return fail(c, ENOAO_ENOMEM, "re-decision list not allocated");
   for (int d = 0; d < nd; ++d) {
@@ -1202,6 +1259,37 @@ int enoao_uses_grid_redecide(const enoao_ctx* c) { return c && use_list(c) ? 1 :
 enoao_status enoao_set_tma(enoao_ctx* c, int on) {
   if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
   c->tma = on ? 1 : 0;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return ENOAO_OK;
+}
+
+enoao_status enoao_set_fused_stage(enoao_ctx* c, int on, int x_lines, int x_cells, int y_lines,
+                                   int y_cells) {
+  if (!c) return fail(c, ENOAO_EINVAL, "NULL context");
+  if (c->batch) return fail(c, ENOAO_EINVAL, "not available for batched contexts");
+  if (on != 0 && on != 1) return fail(c, ENOAO_EINVAL, "on must be 0 or 1");
+  if (on) {
+    if (c->cfg.ndim != 2) return fail(c, ENOAO_EINVAL, "the fused stage is for 2D problems");
+    if (x_lines == 0 && x_cells == 0 && y_lines == 0 && y_cells == 0) {
+      x_lines = c->fused_tiles[0], x_cells = c->fused_tiles[1];
+      y_lines = c->fused_tiles[2], y_cells = c->fused_tiles[3];
+    }
+    enoao_status r = check_tiles(c, 0, x_lines, x_cells);
+    if (r != ENOAO_OK) return r;
+    r = check_tiles(c, 1, y_lines, y_cells);
+    if (r != ENOAO_OK) return r;
+    if (y_cells % x_lines != 0 || x_cells % y_lines != 0)
+      return fail(c, ENOAO_EINVAL,
+                  "fused tiles: y cells (%d) must be a multiple of x lines (%d) and x cells (%d) "
+                  "of y lines (%d)",
+                  y_cells, x_lines, x_cells, y_lines);
+    c->fused_tiles[0] = x_lines, c->fused_tiles[1] = x_cells;
+    c->fused_tiles[2] = y_lines, c->fused_tiles[3] = y_cells;
+  }
+  c->fused = on;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;

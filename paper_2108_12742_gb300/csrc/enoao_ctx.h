@@ -31,6 +31,10 @@ struct enoao_ctx {
   double* U[3] = {nullptr, nullptr, nullptr};  // U^n, U1, U2
   void* rhs = nullptr;
   float* inc[2] = {nullptr, nullptr};  // FP32 bulk: stage increments I0, I1 ([nv][carr])
+  // fused 2D stage (enoao_set_fused_stage): on/off and the tiles of its two
+  // parts (x: lines, cells; y: lines, cells)
+  int fused = 0;
+  int fused_tiles[4] = {4, 64, 8, 48};
   // device scratch of enoao_reconstruct_fluxes with host buffers (grown on demand)
   double* flux_scratch = nullptr;
   size_t flux_scratch_bytes = 0;

@@ -154,6 +154,13 @@ cudaError_t sweep_configure_fp64_field(int nv, int order, size_t smem);
 cudaError_t sweep_configure_fp32_field(int nv, int order, size_t smem);
 cudaError_t sweep_occupancy_fp64_field(int nv, int order, int block, size_t smem, int* per_sm);
 cudaError_t sweep_occupancy_fp32_field(int nv, int order, int block, size_t smem, int* per_sm);
+// the fused 2D stage kernel (both axes in one launch; FP32 bulk, nv 1 or 4):
+// ax the x sweep's arguments, ay the y sweep's; lean: the seven-block ENO-AO5 form
+cudaError_t fused2d_launch_fp32(int nv, int order, const SweepArgs& ax, const SweepArgs& ay,
+                                int grid, int block, size_t smem, cudaStream_t s, int lean);
+cudaError_t fused2d_configure_fp32(int nv, int order, size_t smem, int lean);
+cudaError_t fused2d_occupancy_fp32(int nv, int order, int block, size_t smem, int* per_sm,
+                                   int lean);
 
 // Raises a kernel's dynamic shared-memory limit to at least smem, never
 // lowers it: the limit belongs to the kernel, not to one launch, and the

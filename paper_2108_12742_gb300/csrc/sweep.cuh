@@ -1753,6 +1753,69 @@ constexpr long long kTmaPollLimit = 1ll << 24;
 // the next tile is issued as soon as phase 1 of the current one is done, so
 // it lands while phases 2 and 3 run.  Ghost cells outside the grid (the box
 // reads zeros there) are then filled from the boundary map with plain loads.
+// The end of a sweep launch, for every block: the last block to leave resets
+// the tile queue (and the re-decision epoch), the FP64 re-decision count is
+// added up, and the block's maxima of the new state's speeds go to alpha.
+template <int NV, typename R, bool DEFER, bool FIELD>
+__device__ __forceinline__ void sweep_epilogue(const SweepArgs& A, double (&amax)[kAmax<FIELD>],
+                                               unsigned long long nfall) {
+  constexpr int KA = kAmax<FIELD>;
+  StepState* st = A.st;
+  const int mode = A.mode;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1) {
+      st->tile_next = 0ull;
+      st->blocks_done = 0u;
+      if (DEFER) {
+        // a new tag for the faces this sweep's re-decision pass marks (never 0,
+        // the value of an unmarked face)
+        const unsigned e = st->redo_epoch + 1u;
+        st->redo_epoch = e ? e : 1u;
+      }
+      __threadfence();
+    }
+  }
+
+  if constexpr (sizeof(R) == 4) {
+    if (nfall) atomicAdd(&st->fallbacks, nfall);
+  }
+  if (NV > 1 && (mode & kModeAlpha)) {
+    // block max of |u_d| + c (per field: |u_d - c|, |u_d|, |u_d + c|), then
+    // one atomic per block and value
+    __shared__ double red[KA][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < KA; ++d) {
+      double v = amax[d];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) red[d][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+      for (int d = 0; d < KA; ++d) {
+        double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        unsigned long long* acc;
+        int axis;
+        if constexpr (FIELD) {  // last stage only (per-field runs with per-step alpha)
+          acc = &st->alpha_acc_f[st->par][0][0] + d;
+          axis = d / 3;
+        } else {
+          acc = (A.stage == 2 ? st->alpha_acc[st->par] : st->alpha_stage) + d;
+          axis = d;
+        }
+        if (threadIdx.x == 0 && axis < A.ndim && v > 0.0)
+          atomicMax(acc, (unsigned long long)__double_as_longlong(v));
+      }
+    }
+  }
+}
+
 template <int NV, int ORDER, typename R, bool DEFER = false, bool FIELD = false, bool TMA = false,
           bool LEAN = false>
 __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD, TMA, LEAN>())
@@ -1867,58 +1930,54 @@ __global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, R, FIELD, TMA, LE
                                                           hook);
     }
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1) {
-      st->tile_next = 0ull;
-      st->blocks_done = 0u;
-      if (DEFER) {
-        // a new tag for the faces this sweep's re-decision pass marks (never 0,
-        // the value of an unmarked face)
-        const unsigned e = st->redo_epoch + 1u;
-        st->redo_epoch = e ? e : 1u;
-      }
-      __threadfence();
-    }
-  }
+  sweep_epilogue<NV, R, DEFER, FIELD>(A, amax, nfall);
+}
 
-  if constexpr (FP32) {
-    if (nfall) atomicAdd(&st->fallbacks, nfall);
-  }
-  if (NV > 1 && (mode & kModeAlpha)) {
-    // block max of |u_d| + c (per field: |u_d - c|, |u_d|, |u_d + c|), then
-    // one atomic per block and value
-    __shared__ double red[KA][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int d = 0; d < KA; ++d) {
-      double v = amax[d];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-      if (lane == 0) red[d][wid] = v;
-    }
+// One Runge-Kutta stage of a 2D problem in one launch (FP32 bulk, one alpha,
+// in-sweep re-decisions; Sec. 2's unsplit sum of the two axes' flux
+// differences).  A block takes a 2D tile of Ax.ts x Ay.ts cells: first the x
+// part of L(u) on it, as sub-tiles of Ax.ta rows that store it in the
+// right-hand-side array like the x sweep, then, after the barrier that ends
+// every sub-tile, the y part as sub-tiles of Ay.ta columns that add the
+// stored x part and combine, like the y sweep.  A cell's x part is read back
+// only by the block that wrote it, straight after writing it (from L2), so
+// blocks never wait on one another.  Ax and Ay are the two axes' arguments
+// as separate launches would take them; the host makes the 2D tile a whole
+// number of both axes' sub-tiles (Ay.ts % Ax.ta == 0, Ax.ts % Ay.ta == 0).
+template <int NV, int ORDER, bool LEAN>
+__global__ void __launch_bounds__(128, sweep_min_blocks<ORDER, float, false, false, LEAN>())
+    fused2d_kernel(const __grid_constant__ SweepArgs Ax, const __grid_constant__ SweepArgs Ay) {
+  using R = float;
+  StepState* st = Ay.st;
+  if (st->skip) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const double alpha_x = st->alpha[0], alpha_y = st->alpha[1];
+  const double dt = st->dt;
+  double amax[3] = {0.0, 0.0, 0.0};
+  unsigned long long nfall = 0;
+  const long long tx = Ax.tiles_s, ty = Ay.tiles_s;  // 2D tiles along x and y
+  const int kx = Ay.ts / Ax.ta, ky = Ax.ts / Ay.ta;   // sub-tiles per 2D tile
+  __shared__ long long s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(&st->tile_next, 1ull);
     __syncthreads();
-    if (threadIdx.x < 32) {
-      const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-      for (int d = 0; d < KA; ++d) {
-        double v = threadIdx.x < nw ? red[d][threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        unsigned long long* acc;
-        int axis;
-        if constexpr (FIELD) {  // last stage only (per-field runs with per-step alpha)
-          acc = &st->alpha_acc_f[st->par][0][0] + d;
-          axis = d / 3;
-        } else {
-          acc = (A.stage == 2 ? st->alpha_acc[st->par] : st->alpha_stage) + d;
-          axis = d;
-        }
-        if (threadIdx.x == 0 && axis < A.ndim && v > 0.0)
-          atomicMax(acc, (unsigned long long)__double_as_longlong(v));
-      }
+    const long long T = s_tile;
+    if (T >= tx * ty) break;
+    const long long X = T % tx, Y = T / tx;
+    for (int k = 0; k < kx; ++k) {
+      const long long rows = Y * kx + k;  // row group of Ax.ta rows
+      if (rows >= Ax.tiles_a) break;
+      sweep_tile<NV, ORDER, R, false, false, false, false, NoHook, LEAN>(
+          Ax, tile_geo(Ax, X + Ax.tiles_s * rows), smem_raw, alpha_x, dt, amax, nfall);
+    }
+    for (int m = 0; m < ky; ++m) {
+      const long long cols = X * ky + m;  // column group of Ay.ta columns
+      if (cols >= Ay.tiles_a) break;
+      sweep_tile<NV, ORDER, R, false, false, false, false, NoHook, LEAN>(
+          Ay, tile_geo(Ay, Y + Ay.tiles_s * cols), smem_raw, alpha_y, dt, amax, nfall);
     }
   }
+  sweep_epilogue<NV, R, false, false>(Ay, amax, nfall);
 }
 
 // ------------------------------------------------ grid-wide FP64 re-decisions
