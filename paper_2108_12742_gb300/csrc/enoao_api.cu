@@ -296,12 +296,15 @@ int halo(int order) { return order / 2 + 2; }
 void default_tiles(enoao_ctx* c) {
   const bool f32 = fp32(c);
   for (int d = 0; d < c->cfg.ndim; ++d) {
+    // FP32 2D ENO-AO5: 2 x 191 (x) and 8 x 31 (y) tiles take the LEAN kernel
+    // at eight blocks per SM (measured fastest on 4096^2 Euler data)
+    const bool lean2d = f32 && c->cfg.ndim == 2 && c->cfg.order == 5;
     if (d == 0) {
-      c->ta[d] = c->cfg.ndim == 1 ? 1 : 4;
-      c->ts[d] = 63;
+      c->ta[d] = c->cfg.ndim == 1 ? 1 : (lean2d ? 2 : 4);
+      c->ts[d] = lean2d ? 191 : 63;
     } else {
       c->ta[d] = f32 ? 8 : 32;
-      c->ts[d] = f32 ? 47 : 15;  // FP32 2D Euler: six 30 KB blocks per SM, 17 % halo
+      c->ts[d] = f32 ? (lean2d ? 31 : 47) : 15;
     }
     c->block[d] = 128;
   }
@@ -510,8 +513,8 @@ enoao_status launch_sweep(enoao_ctx* c, int d, int stage, int mode, const double
   const int nv = c->nv, order = c->cfg.order;
   a.field = consts(c).field;
   if (fp32(c)) {
-    // ENO-AO5 tiles that let seven blocks share an SM take the LEAN kernel
-    // (re-decisions out of line, 72 registers); measured faster there
+    // ENO-AO5 tiles that let seven (or eight) blocks share an SM take the
+    // LEAN kernel (re-decisions out of line, 64 registers); measured faster there
     if (!a.field && !list && !tma && order == 5 && smem * 7 <= 220 * 1024) {
       int lean_per_sm = 0;
       if (sweep_configure_fp32(nv, order, smem, 2) == cudaSuccess &&
@@ -1377,7 +1380,7 @@ enoao_status enoao_autotune(enoao_ctx* c) {
     std::vector<std::pair<int, int>> cands;
     if (d == 0) {
       const int tas[] = {1, 2, 4, 8};
-      const int tss[] = {31, 63, 127, 255};
+      const int tss[] = {31, 63, 127, 159, 191, 255};
       for (int ta : tas)
         for (int ts : tss)
           if (c->cfg.ndim > 1 || ta == 1) cands.push_back({ta, ts});
@@ -1394,7 +1397,11 @@ enoao_status enoao_autotune(enoao_ctx* c) {
       if (check_tiles(c, d, p.first, p.second) != ENOAO_OK) continue;
       c->ta[d] = p.first;
       c->ts[d] = p.second;
-      const int mode = kModeCombine;  // stage 0 into U1; the live state U^n is untouched
+      // the mode of the axis in a step's stage 0 (earlier axes store L(u), the
+      // last adds it and combines into U1); the live state U^n is untouched
+      const int nd = c->cfg.ndim;
+      const int mode = d < nd - 1 ? (kModeRhsStore | (d > 0 ? kModeRhsAdd : 0))
+                                  : (kModeCombine | (nd > 1 ? kModeRhsAdd : 0));
       alpha_current_kernel<<<1, 1, 0, c->s>>>(c->st, consts(c));
       r = launch_sweep(c, d, 0, mode, c->U[2], c->U[1], nullptr, nullptr, list);  // warm-up
       if (r != ENOAO_OK) continue;

@@ -1730,14 +1730,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& A, const TileGeo& g,
 // With a TMA-staged raw tile a block needs more shared memory, and four of
 // them fill an SM: they get the registers (128, no spills; at 96 the
 // thread-0 copy issue spills).
-// LEAN (ENO-AO5 in-sweep re-decision, re-decisions out of line): seven
-// blocks, 72 registers, for tiles whose shared memory lets seven fit.
+// LEAN (ENO-AO5 in-sweep re-decision, re-decisions out of line): 64
+// registers (no more spills than at 72), for tiles whose shared memory lets
+// seven or eight blocks share an SM.
 template <int ORDER, typename R, bool FIELD = false, bool TMA = false, bool LEAN = false>
 constexpr int sweep_min_blocks() {
   return sizeof(R) == 8 ? 1
                         : (FIELD ? 4
                                  : (TMA ? 4
-                                        : (LEAN ? 7
+                                        : (LEAN ? 8
                                                 : (ORDER == 5 ? ENOAO_FP32_MIN_BLOCKS_AO5
                                                               : ENOAO_FP32_MIN_BLOCKS_AO7))));
 }
