@@ -57,11 +57,18 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return r;
 }
 
-// Three resident blocks of 256 threads per SM asked of the compiler (80
-// registers, a few spilled): 4096 uneven FP32-bulk problems 1.52e10 ->
-// 1.68e10 cell-stage/s against the unbounded 116 registers and two blocks.
+// Resident 256-thread blocks per SM asked of the compiler: FP32 bulk four
+// (64 registers, some spilled), FP64 three (80).  4096 uneven problems,
+// against the unbounded 116 registers and two blocks: FP32 bulk 1.52e10 ->
+// 1.68e10 (three) -> 1.73e10 (four) cell-stage/s; FP64 1.37e9 at three,
+// 1.30e9 at four.
+template <typename R>
+constexpr int batch_min_blocks() {
+  return sizeof(R) == 4 ? 4 : 3;
+}
+
 template <int NV, int ORDER, typename R>
-__global__ void __launch_bounds__(256, 3) batch_kernel(const BatchArgs B) {
+__global__ void __launch_bounds__(256, batch_min_blocks<R>()) batch_kernel(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_q;
   __shared__ double s_red[32];
